@@ -1,0 +1,129 @@
+/*
+ * tmhop.h -- C ABI of the GB300 (sm_103a) library for the even-odd
+ * preconditioned Wilson twisted-mass operator.
+ *
+ * The operator is the one whose hopping matrix the tmLQCD suite optimises
+ * (arXiv:1311.4521, Sec. 1-2: "Hopping_Matrix", full- and half-spinor
+ * kernels, "Dirac matrix inversion" by the inverter), in the standard
+ * hopping-parameter form:
+ *
+ *   Dhop psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                      + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)
+ *   H_eo, H_oe  = Dhop from odd to even / even to odd sites
+ *   Q_tm        = gamma5 [ (1 + i mut gamma5) - kappa^2 H_eo (1 + i mut gamma5)^-1 H_oe ],
+ *                 mut = 2 kappa mu
+ *
+ * in the chiral gamma basis (gamma5 = diag(1,1,-1,-1)); direction 0 is
+ * time.  A hop that wraps around the lattice in direction mu is multiplied
+ * by bc[mu] (+1 periodic, -1 antiperiodic).
+ *
+ * Conventions for every entry point:
+ *   - dims[4] = {Lx, Ly, Lz, Lt}; every extent even and >= 2, else
+ *     TM_ERR_ARG.  Sites are lex = x + Lx*(y + Ly*(z + Lz*t)); parity
+ *     (x+y+z+t) mod 2; a one-parity field holds its Vh = V/2 sites at index
+ *     lex/2.
+ *   - Pointers named *_dev are device memory of the context's device,
+ *     owned by the caller, 16-byte aligned, and not overlapping unless
+ *     stated.  Host pointers are named *_host.
+ *   - "Packed" spinor fields are the library's storage of one parity in a
+ *     given precision (component-major, see tm_spinor_bytes); they are
+ *     produced by tm_spinor_pack and read back by tm_spinor_unpack.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous unless stated.  Arguments are validated
+ *     on the host before anything is launched.
+ *   - Errors are returned as tm_status, never thrown; tm_last_error gives
+ *     the message of the most recent failure on that context.
+ */
+#ifndef TMHOP_H
+#define TMHOP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tm_ctx tm_ctx;
+typedef struct tm_gauge tm_gauge;
+
+typedef enum {
+    TM_OK = 0,
+    TM_ERR_ARG = 1,            /* invalid argument (null pointer, odd extent, bad enum ...) */
+    TM_ERR_CUDA = 2,           /* a CUDA runtime call failed; message in tm_last_error */
+    TM_ERR_NOT_CONVERGED = 3,  /* solver reached maxiter; x holds the last iterate */
+    TM_ERR_NONFINITE = 4,      /* NaN or Inf met in a residual norm */
+    TM_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    TM_ERR_UNSUPPORTED = 6     /* valid but not implemented combination */
+} tm_status;
+
+typedef enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2 } tm_prec;
+
+enum { TM_EO = 0,   /* output even sites, input odd sites: H_eo */
+       TM_OE = 1 }; /* output odd sites, input even sites: H_oe */
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` (which becomes current).  The
+ * context owns scratch buffers and tuning results; one context serves one
+ * host thread at a time. */
+tm_status tm_ctx_create(tm_ctx **ctx, int device);
+void tm_ctx_destroy(tm_ctx *ctx);
+/* Message of the last failure on ctx (never NULL; "" if none). */
+const char *tm_last_error(const tm_ctx *ctx);
+const char *tm_status_string(tm_status s);
+
+/* ---- fields --------------------------------------------------------------- */
+
+/* Bytes of one packed one-parity spinor field of Vh sites in precision prec:
+ *   TM_F64: 12 arrays of Vh double2 (one per spin-colour component)   192*Vh
+ *   TM_F32:  6 arrays of Vh float4  (two components each)              96*Vh
+ *   TM_F16:  3 arrays of Vh x 8 halves (four components each, scaled by
+ *            the site norm) followed by Vh floats (the site norm = max |re|,|im|) 52*Vh
+ * Returns 0 for an invalid prec. */
+size_t tm_spinor_bytes(long vh, int prec);
+
+/* Packs Vh spinors given as complex double [Vh][4][3] (re, im interleaved)
+ * into the packed layout of precision prec.  in_dev and out_dev must not
+ * overlap. */
+tm_status tm_spinor_pack(tm_ctx *ctx, long vh, const double *in_dev, void *out_dev, int prec, void *stream);
+/* Inverse of tm_spinor_pack: packed field -> complex double [Vh][4][3]. */
+tm_status tm_spinor_unpack(tm_ctx *ctx, long vh, const void *in_dev, double *out_dev, int prec, void *stream);
+
+/* ---- gauge field -------------------------------------------------------- */
+
+/* Builds the library's storage of a gauge field from U_dev, complex double
+ * [4][V][3][3] (mu = 0 is time, then x, y, z; row-major 3x3).  prec is the
+ * storage precision; reconstruct 18 stores all nine complex entries, 12
+ * stores two rows and rebuilds the third as conj(row0 x row1), which is
+ * exact for SU(3) links only (TM_F16 requires 12).  bc[mu] in {+1,-1} is
+ * the boundary sign of direction mu.  The handle owns its device memory
+ * and keeps no reference to U_dev.  Synchronous with respect to stream. */
+tm_status tm_gauge_create(tm_ctx *ctx, const int dims[4], const double *U_dev, int prec, int reconstruct,
+                          const int bc[4], void *stream, tm_gauge **out);
+void tm_gauge_destroy(tm_gauge *g);
+/* Bytes of device memory held by the handle's link storage. */
+size_t tm_gauge_bytes(const tm_gauge *g);
+
+/* ---- operator ------------------------------------------------------------ */
+
+/* out = H psi for dir TM_EO (H_eo: odd in, even out) or TM_OE (H_oe: even
+ * in, odd out); dagger != 0 applies H^dagger instead, i.e. the hop with
+ * both spin projectors swapped (gamma5 H gamma5 of the opposite direction).
+ * Fields are packed in the gauge handle's precision; out and in must not
+ * overlap. */
+tm_status tm_hopping_eo(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const void *in_dev, int dir, int dagger,
+                        void *stream);
+
+/* out_e = Q_tm(sign*mu) in_e on even sites, packed in the gauge handle's
+ * precision.  sign = +1 gives Q(mu), sign = -1 gives Q(-mu) = Q(mu)^dagger.
+ * Two launches: tmp_o = (1 + i mut gamma5)^-1 H_oe in_e into a scratch odd
+ * field owned by ctx, then the fused even update.  out_e and in_e must not
+ * overlap. */
+tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in_e_dev, double kappa, double mu,
+                 int sign, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMHOP_H */

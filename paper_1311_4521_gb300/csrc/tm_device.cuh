@@ -1,0 +1,489 @@
+// tm_device.cuh -- per-site building blocks of the hopping matrix on sm_103a.
+//
+// One output site per thread, pull form: every site gathers its eight
+// neighbours, so no two threads write the same memory and no atomics are
+// needed (the race-free alternative to the push loops with "critical",
+// "atomic" or per-site "halo memory" discussed in Sec. 2.4 of the paper).
+// Neighbour indices are computed arithmetically from the even-odd index
+// instead of being read from the g_iup/g_idn/g_hi tables of Sec. 2.2, so
+// index lookups cost no memory traffic at all.
+//
+// The spin structure uses the half-spinor ("Weyl-type") form of Sec. 1:
+// in the chiral basis gamma_mu = [[0, A_mu], [A_mu^dag, 0]] with A_0 = -1,
+// A_k = -i sigma_k, and
+//     (1 + s gamma_mu) psi = ( h , s A_mu^dag h ),   h = u + s A_mu l,
+// where u, l are the upper and lower spin pairs of psi.  Each hop projects
+// to the two-spin h (12 reals), multiplies by the link, and rebuilds the
+// lower pair from the upper one.
+//
+// Everything here is __host__ __device__ so that the same code can be
+// instantiated for a host-side check of the index arithmetic.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define TM_HD __host__ __device__ __forceinline__
+
+namespace twm {
+
+enum { F64 = 0, F32 = 1, F16 = 2 };
+
+// ---------------------------------------------------------------- complex
+template <typename R>
+struct cpx {
+    R re, im;
+};
+
+template <typename R> TM_HD cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> TM_HD cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> TM_HD cpx<R> operator-(cpx<R> a) { return {-a.re, -a.im}; }
+template <typename R> TM_HD cpx<R> operator*(cpx<R> a, cpx<R> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> TM_HD cpx<R> operator*(R s, cpx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R> TM_HD cpx<R> conj(cpx<R> a) { return {a.re, -a.im}; }
+// i*a and -i*a
+template <typename R> TM_HD cpx<R> ti(cpx<R> a) { return {-a.im, a.re}; }
+template <typename R> TM_HD cpx<R> tmi(cpx<R> a) { return {a.im, -a.re}; }
+// acc + a*b and acc + conj(a)*b
+template <typename R> TM_HD cpx<R> cmadd(cpx<R> a, cpx<R> b, cpx<R> acc)
+{
+    acc.re += a.re * b.re;
+    acc.re -= a.im * b.im;
+    acc.im += a.re * b.im;
+    acc.im += a.im * b.re;
+    return acc;
+}
+template <typename R> TM_HD cpx<R> cjmadd(cpx<R> a, cpx<R> b, cpx<R> acc)
+{
+    acc.re += a.re * b.re;
+    acc.re += a.im * b.im;
+    acc.im += a.re * b.im;
+    acc.im -= a.im * b.re;
+    return acc;
+}
+
+template <typename R> using Spinor = cpx<R>[4][3];
+template <typename R> using Half = cpx<R>[2][3];
+template <typename R> using Link = cpx<R>[3][3];
+
+// ---------------------------------------------------------------- geometry
+// Extents and the even-odd strides.  A one-parity field stores site lex at
+// index lex/2; with Lx even, moving by one in y, z or t moves the index by
+// sy = Lx/2, sz = sy*Ly, st = sz*Lz.
+struct Geom {
+    int lx, ly, lz, lt;
+    int hx;                 // lx / 2
+    unsigned vh;            // sites per parity
+    unsigned sy, sz, st;    // index strides of y, z, t
+    int anti[4];            // 1 if a wrapping hop in direction mu (0=t,1=x,2=y,3=z) takes a minus sign
+};
+
+// Neighbour indices (other parity) and wrap flags of output site i of parity p.
+struct Nbrs {
+    unsigned fwd[4], bwd[4];
+    bool wf[4], wb[4];
+};
+
+TM_HD void neighbours(const Geom &g, int p, unsigned i, Nbrs &n)
+{
+    unsigned xh = i % g.hx, r = i / g.hx;
+    unsigned y = r % g.ly;
+    r /= g.ly;
+    unsigned z = r % g.lz;
+    unsigned t = r / g.lz;
+    unsigned x = 2 * xh + ((y + z + t + p) & 1);
+    unsigned row = i - xh;
+    // x
+    n.wf[1] = x == unsigned(g.lx - 1);
+    n.wb[1] = x == 0;
+    n.fwd[1] = row + ((n.wf[1] ? 0u : x + 1) >> 1);
+    n.bwd[1] = row + ((n.wb[1] ? unsigned(g.lx - 1) : x - 1) >> 1);
+    // y
+    n.wf[2] = y == unsigned(g.ly - 1);
+    n.wb[2] = y == 0;
+    n.fwd[2] = n.wf[2] ? i - (g.ly - 1) * g.sy : i + g.sy;
+    n.bwd[2] = n.wb[2] ? i + (g.ly - 1) * g.sy : i - g.sy;
+    // z
+    n.wf[3] = z == unsigned(g.lz - 1);
+    n.wb[3] = z == 0;
+    n.fwd[3] = n.wf[3] ? i - (g.lz - 1) * g.sz : i + g.sz;
+    n.bwd[3] = n.wb[3] ? i + (g.lz - 1) * g.sz : i - g.sz;
+    // t
+    n.wf[0] = t == unsigned(g.lt - 1);
+    n.wb[0] = t == 0;
+    n.fwd[0] = n.wf[0] ? i - (g.lt - 1) * g.st : i + g.st;
+    n.bwd[0] = n.wb[0] ? i + (g.lt - 1) * g.st : i - g.st;
+}
+
+// ---------------------------------------------------------------- loads
+#if defined(__CUDA_ARCH__)
+template <typename T> __device__ __forceinline__ T ld_keep(const T *p) { return __ldg(p); }
+template <typename T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+template <typename T> __device__ __forceinline__ void st_stream(T *p, T v) { __stcs(p, v); }
+#else
+template <typename T> inline T ld_keep(const T *p) { return *p; }
+template <typename T> inline T ld_stream(const T *p) { return *p; }
+template <typename T> inline void st_stream(T *p, T v) { *p = v; }
+#endif
+
+// Spinor storage of one parity (component-major, Vh sites per array).
+template <int P> struct SpinorIO;
+
+template <> struct SpinorIO<F64> {
+    using R = double;
+    TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        const double2 *b = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 v = ld_keep(b + size_t(c) * vh + i);
+            s[c / 3][c % 3] = {v.x, v.y};
+        }
+    }
+    TM_HD static void store(void *base, unsigned vh, unsigned i, const Spinor<R> &s)
+    {
+        double2 *b = static_cast<double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) st_stream(b + size_t(c) * vh + i, make_double2(s[c / 3][c % 3].re, s[c / 3][c % 3].im));
+    }
+};
+
+template <> struct SpinorIO<F32> {
+    using R = float;
+    TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        const float4 *b = static_cast<const float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 v = ld_keep(b + size_t(k) * vh + i);
+            s[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
+            s[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
+        }
+    }
+    TM_HD static void store(void *base, unsigned vh, unsigned i, const Spinor<R> &s)
+    {
+        float4 *b = static_cast<float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const cpx<R> &a = s[(2 * k) / 3][(2 * k) % 3];
+            const cpx<R> &c = s[(2 * k + 1) / 3][(2 * k + 1) % 3];
+            st_stream(b + size_t(k) * vh + i, make_float4(a.re, a.im, c.re, c.im));
+        }
+    }
+};
+
+// Half precision: each site stores its 24 reals divided by the site norm
+// (the largest |re| or |im|), so every stored value lies in [-1, 1], and the
+// norm itself as a float after the three component arrays.
+template <> struct SpinorIO<F16> {
+    using R = float;
+    TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        const uint4 *b = static_cast<const uint4 *>(base);
+        const float *nrm = reinterpret_cast<const float *>(b + size_t(3) * vh);
+        float n = ld_keep(nrm + i);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v = ld_keep(b + size_t(k) * vh + i);
+            unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __half2 h = *reinterpret_cast<__half2 *>(&w[q]);
+                float2 f = __half22float2(h);
+                int c = 4 * k + q;
+                s[c / 3][c % 3] = {n * f.x, n * f.y};
+            }
+        }
+    }
+    TM_HD static void store(void *base, unsigned vh, unsigned i, const Spinor<R> &s)
+    {
+        uint4 *b = static_cast<uint4 *>(base);
+        float *nrm = reinterpret_cast<float *>(b + size_t(3) * vh);
+        float n = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) n = fmaxf(n, fmaxf(fabsf(s[c / 3][c % 3].re), fabsf(s[c / 3][c % 3].im)));
+        float inv = n > 0.f ? 1.f / n : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            unsigned w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int c = 4 * k + q;
+                __half2 h = __floats2half2_rn(s[c / 3][c % 3].re * inv, s[c / 3][c % 3].im * inv);
+                w[q] = *reinterpret_cast<unsigned *>(&h);
+            }
+            st_stream(b + size_t(k) * vh + i, make_uint4(w[0], w[1], w[2], w[3]));
+        }
+        st_stream(nrm + i, n);
+    }
+};
+
+// Bytes of one packed parity field.
+TM_HD size_t spinor_bytes(unsigned vh, int prec)
+{
+    return prec == F64 ? size_t(192) * vh : prec == F32 ? size_t(96) * vh : prec == F16 ? size_t(52) * vh : 0;
+}
+
+// Link storage: for each origin parity p and direction mu a block of NCHUNK
+// arrays of Vh vectors, block index 4p + mu.  Reconstruct 12 keeps rows 0
+// and 1; row 2 of an SU(3) matrix is conj(row0 x row1).
+template <typename R> TM_HD void reconstruct_row2(Link<R> &u)
+{
+    u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+    u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+    u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+}
+
+template <int P, int RECON> struct LinkIO;
+
+template <> struct LinkIO<F64, 18> {
+    using R = double;
+    using V = double2;
+    static constexpr int NCHUNK = 9;
+    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            V v = ld_stream(blk + size_t(k) * vh + i);
+            u[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
+    TM_HD static void store(V *blk, unsigned vh, unsigned i, const double *m)
+    {
+        for (int k = 0; k < 9; ++k) blk[size_t(k) * vh + i] = make_double2(m[2 * k], m[2 * k + 1]);
+    }
+};
+
+template <> struct LinkIO<F64, 12> {
+    using R = double;
+    using V = double2;
+    static constexpr int NCHUNK = 6;
+    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            V v = ld_stream(blk + size_t(k) * vh + i);
+            u[k / 3][k % 3] = {v.x, v.y};
+        }
+        reconstruct_row2(u);
+    }
+    TM_HD static void store(V *blk, unsigned vh, unsigned i, const double *m)
+    {
+        for (int k = 0; k < 6; ++k) blk[size_t(k) * vh + i] = make_double2(m[2 * k], m[2 * k + 1]);
+    }
+};
+
+template <> struct LinkIO<F32, 18> {
+    using R = float;
+    using V = float2;
+    static constexpr int NCHUNK = 9;
+    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            V v = ld_stream(blk + size_t(k) * vh + i);
+            u[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
+    TM_HD static void store(V *blk, unsigned vh, unsigned i, const double *m)
+    {
+        for (int k = 0; k < 9; ++k) blk[size_t(k) * vh + i] = make_float2(float(m[2 * k]), float(m[2 * k + 1]));
+    }
+};
+
+template <> struct LinkIO<F32, 12> {
+    using R = float;
+    using V = float4;
+    static constexpr int NCHUNK = 3;
+    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V v = ld_stream(blk + size_t(k) * vh + i);
+            u[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
+            u[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
+        }
+        reconstruct_row2(u);
+    }
+    TM_HD static void store(V *blk, unsigned vh, unsigned i, const double *m)
+    {
+        for (int k = 0; k < 3; ++k)
+            blk[size_t(k) * vh + i] = make_float4(float(m[4 * k]), float(m[4 * k + 1]), float(m[4 * k + 2]), float(m[4 * k + 3]));
+    }
+};
+
+// Half-precision links: entries of an SU(3) matrix lie in [-1, 1], so no scale is stored.
+template <> struct LinkIO<F16, 12> {
+    using R = float;
+    using V = uint2;
+    static constexpr int NCHUNK = 3;
+    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V v = ld_stream(blk + size_t(k) * vh + i);
+            float2 a = __half22float2(*reinterpret_cast<__half2 *>(&v.x));
+            float2 b = __half22float2(*reinterpret_cast<__half2 *>(&v.y));
+            u[(2 * k) / 3][(2 * k) % 3] = {a.x, a.y};
+            u[(2 * k + 1) / 3][(2 * k + 1) % 3] = {b.x, b.y};
+        }
+        reconstruct_row2(u);
+    }
+    TM_HD static void store(V *blk, unsigned vh, unsigned i, const double *m)
+    {
+        for (int k = 0; k < 3; ++k) {
+            __half2 a = __floats2half2_rn(float(m[4 * k]), float(m[4 * k + 1]));
+            __half2 b = __floats2half2_rn(float(m[4 * k + 2]), float(m[4 * k + 3]));
+            blk[size_t(k) * vh + i] = make_uint2(*reinterpret_cast<unsigned *>(&a), *reinterpret_cast<unsigned *>(&b));
+        }
+    }
+};
+
+// ---------------------------------------------------------------- spin algebra
+// h = u + s A_mu l  (the upper pair of (1 + s gamma_mu) psi), s = +1 or -1.
+template <int MU, int S, typename R> TM_HD void project(const Spinor<R> &p, Half<R> &h)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (MU == 0) {  // A_0 l = (-l0, -l1)
+            h[0][c] = S > 0 ? p[0][c] - p[2][c] : p[0][c] + p[2][c];
+            h[1][c] = S > 0 ? p[1][c] - p[3][c] : p[1][c] + p[3][c];
+        } else if (MU == 1) {  // A_1 l = (-i l1, -i l0)
+            h[0][c] = S > 0 ? p[0][c] + tmi(p[3][c]) : p[0][c] + ti(p[3][c]);
+            h[1][c] = S > 0 ? p[1][c] + tmi(p[2][c]) : p[1][c] + ti(p[2][c]);
+        } else if (MU == 2) {  // A_2 l = (-l1, l0)
+            h[0][c] = S > 0 ? p[0][c] - p[3][c] : p[0][c] + p[3][c];
+            h[1][c] = S > 0 ? p[1][c] + p[2][c] : p[1][c] - p[2][c];
+        } else {  // A_3 l = (-i l0, i l1)
+            h[0][c] = S > 0 ? p[0][c] + tmi(p[2][c]) : p[0][c] + ti(p[2][c]);
+            h[1][c] = S > 0 ? p[1][c] + ti(p[3][c]) : p[1][c] + tmi(p[3][c]);
+        }
+    }
+}
+
+// acc += (h, s A_mu^dag h), the full spinor rebuilt from its upper pair.
+template <int MU, int S, typename R> TM_HD void accumulate(const Half<R> &h, Spinor<R> &a)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[0][c] = a[0][c] + h[0][c];
+        a[1][c] = a[1][c] + h[1][c];
+        if (MU == 0) {  // A_0^dag h = (-h0, -h1)
+            a[2][c] = S > 0 ? a[2][c] - h[0][c] : a[2][c] + h[0][c];
+            a[3][c] = S > 0 ? a[3][c] - h[1][c] : a[3][c] + h[1][c];
+        } else if (MU == 1) {  // A_1^dag h = (i h1, i h0)
+            a[2][c] = S > 0 ? a[2][c] + ti(h[1][c]) : a[2][c] + tmi(h[1][c]);
+            a[3][c] = S > 0 ? a[3][c] + ti(h[0][c]) : a[3][c] + tmi(h[0][c]);
+        } else if (MU == 2) {  // A_2^dag h = (h1, -h0)
+            a[2][c] = S > 0 ? a[2][c] + h[1][c] : a[2][c] - h[1][c];
+            a[3][c] = S > 0 ? a[3][c] - h[0][c] : a[3][c] + h[0][c];
+        } else {  // A_3^dag h = (i h0, -i h1)
+            a[2][c] = S > 0 ? a[2][c] + ti(h[0][c]) : a[2][c] + tmi(h[0][c]);
+            a[3][c] = S > 0 ? a[3][c] + tmi(h[1][c]) : a[3][c] + ti(h[1][c]);
+        }
+    }
+}
+
+// r = U h (dag = false) or U^dag h (dag = true) on both spin components.
+template <bool DAG, typename R> TM_HD void link_mul(const Link<R> &u, const Half<R> &h, Half<R> &r)
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cpx<R> acc = {R(0), R(0)};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) acc = DAG ? cjmadd(u[b][a], h[s][b], acc) : cmadd(u[a][b], h[s][b], acc);
+            r[s][a] = acc;
+        }
+}
+
+template <typename R> TM_HD void negate_half(Half<R> &h)
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[s][c] = -h[s][c];
+}
+
+// One direction mu of the hop at output site i (parity p), added into acc.
+// Forward: (1 - gamma_mu) U_mu(x) psi(x+mu); backward (1 + gamma_mu)
+// U_mu(x-mu)^dag psi(x-mu).  DAG swaps the two projectors, which gives the
+// adjoint hop gamma5 Dhop gamma5 = Dhop^dag.
+template <int P, int RECON, bool DAG, int MU>
+TM_HD void hop_dir(const Geom &g, int p, unsigned i, const Nbrs &n, const typename LinkIO<P, RECON>::V *links,
+                   const void *in, Spinor<typename SpinorIO<P>::R> &acc)
+{
+    using R = typename SpinorIO<P>::R;
+    using L = LinkIO<P, RECON>;
+    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
+    constexpr int SB = -SF;
+    const size_t blk = size_t(L::NCHUNK) * g.vh;
+    {
+        Spinor<R> s;
+        Half<R> h, r;
+        Link<R> u;
+        SpinorIO<P>::load(in, g.vh, n.fwd[MU], s);
+        project<MU, SF>(s, h);
+        L::load(links + (4 * p + MU) * blk, g.vh, i, u);
+        link_mul<false>(u, h, r);
+        if (n.wf[MU] && g.anti[MU]) negate_half(r);
+        accumulate<MU, SF>(r, acc);
+    }
+    {
+        Spinor<R> s;
+        Half<R> h, r;
+        Link<R> u;
+        SpinorIO<P>::load(in, g.vh, n.bwd[MU], s);
+        project<MU, SB>(s, h);
+        L::load(links + (4 * (1 - p) + MU) * blk, g.vh, n.bwd[MU], u);
+        link_mul<true>(u, h, r);
+        if (n.wb[MU] && g.anti[MU]) negate_half(r);
+        accumulate<MU, SB>(r, acc);
+    }
+}
+
+template <int P, int RECON, bool DAG>
+TM_HD void hop_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, RECON>::V *links, const void *in,
+                    Spinor<typename SpinorIO<P>::R> &acc)
+{
+    using R = typename SpinorIO<P>::R;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[s][c] = {R(0), R(0)};
+    Nbrs n;
+    neighbours(g, p, i, n);
+    hop_dir<P, RECON, DAG, 0>(g, p, i, n, links, in, acc);
+    hop_dir<P, RECON, DAG, 1>(g, p, i, n, links, in, acc);
+    hop_dir<P, RECON, DAG, 2>(g, p, i, n, links, in, acc);
+    hop_dir<P, RECON, DAG, 3>(g, p, i, n, links, in, acc);
+}
+
+// Site-local epilogue: out_u = a_u hop_u + b_u x_u, out_l = a_l hop_l + b_l x_l
+// (u = spins 0,1; l = spins 2,3).  With gamma5 = diag(1,1,-1,-1) this covers
+// the twisted-mass factors (1 +- i mut gamma5)^(+-1) and the final gamma5.
+struct Coef {
+    double au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im;
+};
+
+template <typename R> TM_HD void epilogue(const Coef &k, const Spinor<R> &hop, const Spinor<R> *x, Spinor<R> &out)
+{
+    cpx<R> au = {R(k.au_re), R(k.au_im)}, al = {R(k.al_re), R(k.al_im)};
+    cpx<R> bu = {R(k.bu_re), R(k.bu_im)}, bl = {R(k.bl_re), R(k.bl_im)};
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cpx<R> a = s < 2 ? au : al;
+            cpx<R> v = a * hop[s][c];
+            if (x) v = cmadd(s < 2 ? bu : bl, (*x)[s][c], v);
+            out[s][c] = v;
+        }
+}
+
+}  // namespace twm

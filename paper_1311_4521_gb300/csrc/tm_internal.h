@@ -1,0 +1,53 @@
+// tm_internal.h -- host-side structures and launcher declarations shared by
+// the library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "tm_device.cuh"
+#include "tmhop.h"
+
+struct tm_ctx {
+    int device = 0;
+    std::string err;
+    void *scratch = nullptr;       // odd-parity temporaries of Q_tm and friends
+    size_t scratch_bytes = 0;
+    int sm_count = 0;
+};
+
+struct tm_gauge {
+    tm_ctx *ctx = nullptr;
+    int dims[4] = {0, 0, 0, 0};
+    int bc[4] = {1, 1, 1, 1};
+    int prec = 0;
+    int recon = 18;
+    twm::Geom geom{};
+    void *links = nullptr;
+    size_t bytes = 0;
+};
+
+namespace twm {
+
+// Fills the geometry of a lattice; returns false if the extents are invalid.
+bool make_geom(const int dims[4], const int bc[4], Geom &g);
+
+// Launchers (tm_kernels.cu).  All enqueue on `s` and return the launch status.
+cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_parity, const void *links,
+                       const void *in, void *out, const void *x, const Coef &k, cudaStream_t s, int block);
+cudaError_t launch_pack_gauge(const Geom &g, int prec, int recon, const double *U, void *links, cudaStream_t s);
+cudaError_t launch_pack_spinor(unsigned vh, int prec, const double *in, void *out, cudaStream_t s);
+cudaError_t launch_unpack_spinor(unsigned vh, int prec, const void *in, double *out, cudaStream_t s);
+size_t link_chunk_bytes(int prec, int recon);
+int link_nchunk(int prec, int recon);
+
+// Coefficients of the two Q_tm launches (see tm_Qtm): kernel A gives
+// (1 + i mut gamma5)^-1 H_oe in, kernel B gives
+// gamma5 [ (1 + i mut gamma5) in - kappa^2 H_eo tmp ].
+Coef coef_plain();
+Coef coef_qtm_a(double mut);
+Coef coef_qtm_b(double kappa, double mut);
+
+}  // namespace twm

@@ -1,0 +1,195 @@
+// tm_kernels.cu -- hopping-matrix kernels with fused twisted-mass epilogues,
+// and the layout conversions between the canonical complex-double layouts
+// and the packed component-major storage.
+#include "tm_internal.h"
+
+namespace twm {
+
+bool make_geom(const int dims[4], const int bc[4], Geom &g)
+{
+    for (int d = 0; d < 4; ++d)
+        if (dims[d] < 2 || (dims[d] & 1)) return false;
+    double V = double(dims[0]) * dims[1] * dims[2] * dims[3];
+    if (V >= 2147483648.0) return false;
+    g.lx = dims[0];
+    g.ly = dims[1];
+    g.lz = dims[2];
+    g.lt = dims[3];
+    g.hx = dims[0] / 2;
+    g.vh = unsigned(V / 2);
+    g.sy = unsigned(g.hx);
+    g.sz = g.sy * unsigned(g.ly);
+    g.st = g.sz * unsigned(g.lz);
+    for (int m = 0; m < 4; ++m) g.anti[m] = bc ? (bc[m] < 0) : 0;
+    return true;
+}
+
+Coef coef_plain() { return Coef{1, 0, 1, 0, 0, 0, 0, 0}; }
+
+Coef coef_qtm_a(double mut)
+{
+    double d = 1.0 / (1.0 + mut * mut);
+    // (1 - i mut) / (1 + mut^2) on spins 0,1 and (1 + i mut) / (1 + mut^2) on spins 2,3
+    return Coef{d, -mut * d, d, mut * d, 0, 0, 0, 0};
+}
+
+Coef coef_qtm_b(double kappa, double mut)
+{
+    double k2 = kappa * kappa;
+    // upper: -k2 hop + (1 + i mut) x ; lower: -( -k2 hop + (1 - i mut) x )
+    return Coef{-k2, 0, k2, 0, 1.0, mut, -1.0, mut};
+}
+
+// ------------------------------------------------------------------ hop
+template <int P, int RECON, bool DAG, bool HASX>
+__global__ void __launch_bounds__(256) k_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,
+                                             const void *__restrict__ in, void *__restrict__ out,
+                                             const void *__restrict__ x, Coef k)
+{
+    using R = typename SpinorIO<P>::R;
+    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    Spinor<R> acc, o;
+    hop_site<P, RECON, DAG>(g, p, i, links, in, acc);
+    if (HASX) {
+        Spinor<R> xs;
+        SpinorIO<P>::load(x, g.vh, i, xs);
+        epilogue(k, acc, &xs, o);
+    } else {
+        epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
+    }
+    SpinorIO<P>::store(out, g.vh, i, o);
+}
+
+template <int P, int RECON>
+static cudaError_t hop_dispatch(const Geom &g, bool dag, int p, const void *links, const void *in, void *out,
+                                const void *x, const Coef &k, cudaStream_t s, int block)
+{
+    using V = typename LinkIO<P, RECON>::V;
+    const V *l = static_cast<const V *>(links);
+    unsigned grid = (g.vh + block - 1) / block;
+    if (dag) {
+        if (x) k_hop<P, RECON, true, true><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
+        else k_hop<P, RECON, true, false><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
+    } else {
+        if (x) k_hop<P, RECON, false, true><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
+        else k_hop<P, RECON, false, false><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_parity, const void *links,
+                       const void *in, void *out, const void *x, const Coef &k, cudaStream_t s, int block)
+{
+    if (g.vh == 0) return cudaSuccess;
+    if (prec == F64 && recon == 18) return hop_dispatch<F64, 18>(g, dag, out_parity, links, in, out, x, k, s, block);
+    if (prec == F64 && recon == 12) return hop_dispatch<F64, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
+    if (prec == F32 && recon == 18) return hop_dispatch<F32, 18>(g, dag, out_parity, links, in, out, x, k, s, block);
+    if (prec == F32 && recon == 12) return hop_dispatch<F32, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
+    if (prec == F16 && recon == 12) return hop_dispatch<F16, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ layouts
+int link_nchunk(int prec, int recon)
+{
+    if (prec == F64) return recon == 18 ? 9 : 6;
+    if (prec == F32) return recon == 18 ? 9 : 3;
+    if (prec == F16 && recon == 12) return 3;
+    return 0;
+}
+
+size_t link_chunk_bytes(int prec, int recon)
+{
+    if (prec == F64) return 16;
+    if (prec == F32) return recon == 18 ? 8 : 16;
+    if (prec == F16) return 8;
+    return 0;
+}
+
+// One thread per (mu, lexicographic site) of the canonical U[mu][lex][3][3].
+template <int P, int RECON>
+__global__ void k_pack_gauge(Geom g, const double *__restrict__ U, typename LinkIO<P, RECON>::V *links)
+{
+    unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    unsigned long long V = 2ull * g.vh;
+    if (idx >= 4 * V) return;
+    int mu = int(idx / V);
+    unsigned lex = unsigned(idx % V);
+    unsigned x = lex % g.lx, r = lex / g.lx;
+    unsigned y = r % g.ly;
+    r /= g.ly;
+    unsigned z = r % g.lz, t = r / g.lz;
+    int p = (x + y + z + t) & 1;
+    double m[18];
+    for (int k = 0; k < 18; ++k) m[k] = U[idx * 18 + k];
+    using L = LinkIO<P, RECON>;
+    L::store(links + size_t(4 * p + mu) * L::NCHUNK * g.vh, g.vh, lex >> 1, m);
+}
+
+cudaError_t launch_pack_gauge(const Geom &g, int prec, int recon, const double *U, void *links, cudaStream_t s)
+{
+    unsigned long long n = 8ull * g.vh;
+    unsigned grid = unsigned((n + 255) / 256);
+#define TM_PACK(P, RC)                                                                                   \
+    if (prec == P && recon == RC) {                                                                      \
+        k_pack_gauge<P, RC><<<grid, 256, 0, s>>>(g, U, static_cast<typename LinkIO<P, RC>::V *>(links)); \
+        return cudaGetLastError();                                                                       \
+    }
+    TM_PACK(F64, 18)
+    TM_PACK(F64, 12)
+    TM_PACK(F32, 18)
+    TM_PACK(F32, 12)
+    TM_PACK(F16, 12)
+#undef TM_PACK
+    return cudaErrorInvalidValue;
+}
+
+template <int P>
+__global__ void k_pack_spinor(unsigned vh, const double *__restrict__ in, void *out)
+{
+    using R = typename SpinorIO<P>::R;
+    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    Spinor<R> s;
+    for (int c = 0; c < 12; ++c) s[c / 3][c % 3] = {R(in[size_t(i) * 24 + 2 * c]), R(in[size_t(i) * 24 + 2 * c + 1])};
+    SpinorIO<P>::store(out, vh, i, s);
+}
+
+template <int P>
+__global__ void k_unpack_spinor(unsigned vh, const void *in, double *__restrict__ out)
+{
+    using R = typename SpinorIO<P>::R;
+    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    Spinor<R> s;
+    SpinorIO<P>::load(in, vh, i, s);
+    for (int c = 0; c < 12; ++c) {
+        out[size_t(i) * 24 + 2 * c] = double(s[c / 3][c % 3].re);
+        out[size_t(i) * 24 + 2 * c + 1] = double(s[c / 3][c % 3].im);
+    }
+}
+
+cudaError_t launch_pack_spinor(unsigned vh, int prec, const double *in, void *out, cudaStream_t s)
+{
+    if (vh == 0) return cudaSuccess;
+    unsigned grid = (vh + 127) / 128;
+    if (prec == F64) k_pack_spinor<F64><<<grid, 128, 0, s>>>(vh, in, out);
+    else if (prec == F32) k_pack_spinor<F32><<<grid, 128, 0, s>>>(vh, in, out);
+    else if (prec == F16) k_pack_spinor<F16><<<grid, 128, 0, s>>>(vh, in, out);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_spinor(unsigned vh, int prec, const void *in, double *out, cudaStream_t s)
+{
+    if (vh == 0) return cudaSuccess;
+    unsigned grid = (vh + 127) / 128;
+    if (prec == F64) k_unpack_spinor<F64><<<grid, 128, 0, s>>>(vh, in, out);
+    else if (prec == F32) k_unpack_spinor<F32><<<grid, 128, 0, s>>>(vh, in, out);
+    else if (prec == F16) k_unpack_spinor<F16><<<grid, 128, 0, s>>>(vh, in, out);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace twm

@@ -1,0 +1,231 @@
+"""Thin ctypes binding of ``libtmhop.so`` (the C ABI declared in include/tmhop.h).
+
+Functions keep the C names and argument order; they only marshal pointers
+and sizes and turn a non-zero ``tm_status`` into :class:`TmError`.  Every
+step of the computation runs in the library's CUDA kernels.  PyTorch is
+used for device memory and the current stream only.
+
+If the shared library has not been built the import fails loudly: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtmhop.so")
+
+TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE, TM_ERR_TIMEOUT, TM_ERR_UNSUPPORTED = range(7)
+TM_F64, TM_F32, TM_F16 = 0, 1, 2
+TM_EO, TM_OE = 0, 1
+PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16}
+
+
+class TmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1311_4521_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, L, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_size_t
+    I4 = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "tm_ctx_create": ([ctypes.POINTER(P), I], I),
+        "tm_ctx_destroy": ([P], None),
+        "tm_last_error": ([P], ctypes.c_char_p),
+        "tm_status_string": ([I], ctypes.c_char_p),
+        "tm_spinor_bytes": ([L, I], S),
+        "tm_spinor_pack": ([P, L, P, P, I, P], I),
+        "tm_spinor_unpack": ([P, L, P, P, I, P], I),
+        "tm_gauge_create": ([P, I4, P, I, I, I4, P, ctypes.POINTER(P)], I),
+        "tm_gauge_destroy": ([P], None),
+        "tm_gauge_bytes": ([P], S),
+        "tm_hopping_eo": ([P, P, P, P, I, I, P], I),
+        "tm_Qtm": ([P, P, P, P, D, D, I, P], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _i4(v):
+    return (ctypes.c_int * 4)(*[int(a) for a in v])
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t) if t is not None else 0)
+
+
+def _check(ctx_handle, status: int):
+    if status != TM_OK:
+        msg = lib.tm_last_error(ctx_handle).decode() if ctx_handle else ""
+        raise TmError(status, msg or lib.tm_status_string(status).decode())
+
+
+# ---- C-named functions -------------------------------------------------------
+def tm_ctx_create(device: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    st = lib.tm_ctx_create(ctypes.byref(h), int(device))
+    if st != TM_OK:
+        raise TmError(st, f"tm_ctx_create(device={device}): {lib.tm_status_string(st).decode()}")
+    return h
+
+
+def tm_ctx_destroy(ctx) -> None:
+    lib.tm_ctx_destroy(ctx)
+
+
+def tm_last_error(ctx) -> str:
+    return lib.tm_last_error(ctx).decode()
+
+
+def tm_status_string(status: int) -> str:
+    return lib.tm_status_string(int(status)).decode()
+
+
+def tm_spinor_bytes(vh: int, prec: int) -> int:
+    return int(lib.tm_spinor_bytes(int(vh), int(prec)))
+
+
+def tm_spinor_pack(ctx, vh, in_dev, out_dev, prec, stream=None):
+    _check(ctx, lib.tm_spinor_pack(ctx, int(vh), _ptr(in_dev), _ptr(out_dev), int(prec), _stream(stream)))
+
+
+def tm_spinor_unpack(ctx, vh, in_dev, out_dev, prec, stream=None):
+    _check(ctx, lib.tm_spinor_unpack(ctx, int(vh), _ptr(in_dev), _ptr(out_dev), int(prec), _stream(stream)))
+
+
+def tm_gauge_create(ctx, dims, U_dev, prec, reconstruct, bc, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(ctx, lib.tm_gauge_create(ctx, _i4(dims), _ptr(U_dev), int(prec), int(reconstruct), _i4(bc),
+                                    _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def tm_gauge_destroy(g) -> None:
+    lib.tm_gauge_destroy(g)
+
+
+def tm_gauge_bytes(g) -> int:
+    return int(lib.tm_gauge_bytes(g))
+
+
+def tm_hopping_eo(ctx, U, out_dev, in_dev, dir, dagger=0, stream=None):
+    _check(ctx, lib.tm_hopping_eo(ctx, U, _ptr(out_dev), _ptr(in_dev), int(dir), int(dagger), _stream(stream)))
+
+
+def tm_Qtm(ctx, U, out_e_dev, in_e_dev, kappa, mu, sign=1, stream=None):
+    _check(ctx, lib.tm_Qtm(ctx, U, _ptr(out_e_dev), _ptr(in_e_dev), float(kappa), float(mu), int(sign),
+                           _stream(stream)))
+
+
+# ---- convenience layer over torch tensors -----------------------------------------
+class Gauge:
+    """A gauge handle: the library's packed copy of U in one precision."""
+
+    def __init__(self, ctx: "Context", dims, U: torch.Tensor, prec="f64", reconstruct=18, bc=(-1, 1, 1, 1)):
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        self.reconstruct = int(reconstruct)
+        self.bc = tuple(bc)
+        self.vh = int(np.prod(self.dims)) // 2
+        Ur = _as_real_dev(U, ctx.device)
+        self.handle = tm_gauge_create(ctx.handle, self.dims, Ur, self.prec, self.reconstruct, self.bc)
+
+    @property
+    def nbytes(self) -> int:
+        return tm_gauge_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            tm_gauge_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _as_real_dev(t: torch.Tensor, device) -> torch.Tensor:
+    """complex128 tensor -> contiguous float64 view on the device (re, im interleaved)."""
+    if not isinstance(t, torch.Tensor):
+        t = torch.from_numpy(np.ascontiguousarray(t))
+    t = t.to(device=device, dtype=torch.complex128).contiguous()
+    return torch.view_as_real(t).contiguous()
+
+
+class Context:
+    """Owns a ``tm_ctx`` on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.handle = tm_ctx_create(device)
+
+    def close(self):
+        if self.handle:
+            tm_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # fields
+    def gauge(self, dims, U, prec="f64", reconstruct=18, bc=(-1, 1, 1, 1)) -> Gauge:
+        return Gauge(self, dims, U, prec, reconstruct, bc)
+
+    def empty(self, vh: int, prec) -> torch.Tensor:
+        prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        return torch.empty(tm_spinor_bytes(vh, prec), dtype=torch.uint8, device=self.device)
+
+    def pack(self, psi, prec) -> torch.Tensor:
+        """(Vh, 4, 3) complex spinors -> packed field of precision ``prec``."""
+        prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        src = _as_real_dev(psi, self.device)
+        vh = src.shape[0]
+        out = self.empty(vh, prec)
+        tm_spinor_pack(self.handle, vh, src, out, prec)
+        return out
+
+    def unpack(self, buf: torch.Tensor, vh: int, prec) -> torch.Tensor:
+        prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        out = torch.empty((vh, 4, 3, 2), dtype=torch.float64, device=self.device)
+        tm_spinor_unpack(self.handle, vh, buf, out, prec)
+        return torch.view_as_complex(out)
+
+    # operator
+    def hopping_eo(self, U: Gauge, out, inp, dir, dagger=False):
+        tm_hopping_eo(self.handle, U.handle, out, inp, dir, int(bool(dagger)))
+        return out
+
+    def Qtm(self, U: Gauge, out, inp, kappa, mu, sign=1):
+        tm_Qtm(self.handle, U.handle, out, inp, kappa, mu, sign)
+        return out
