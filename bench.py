@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the twisted-mass operator Q_tm on one GB300 per rank.
+
+Workload: the production-size plain FP64 operator, a 32^3x64 lattice with
+near-thermalised links U = exp(0.3 i A) (A Gaussian in su(3)), a Gaussian
+spinor, kappa = 0.1394, mu = 0.0015, antiperiodic in time.  One step is one
+application of Q_tm = gamma5 (M_ee - M_eo M_oo^-1 M_oe) (two fused hop
+launches) with every input already resident in HBM.
+
+Reported per step (one even site = one unit):
+  bytes  algorithmic: each input spinor read once, the 8 links of every
+         output site read, each output written once, plus the re-read of
+         psi_e in the final update (see algo_bytes);
+  flops  1320 per site per hop + 72 + 96 site-local = 2808 per even site.
+
+The JSON line also carries the dominant kernel's roofline (live CUDA-event
+timing of each launch), the FP32/FP16 storage variants, an end-to-end
+number through the C ABI with host buffers, clocks sampled during the timed
+region and the FP64 CPU oracle timed on this host's cores.  With
+``--impl reference`` the oracle alone is timed as the reference arm.
+
+Multi-GPU: replicas only -- every rank applies Q_tm to its own copy of the
+lattice (the operator needs no exchange on one GPU), value = all ranks'
+bytes / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hopping-matrix GB/s & Gflop/s vs HBM roofline; mixed vs FP64 CG time to 1e-10"
+DIMS = (32, 32, 32, 64)
+KAPPA, MU = 0.1394, 0.0015
+SAMPLE_DIMS = (16, 16, 16, 16)       # bounded sample for the CPU reference arm
+L2_BYTES = 129 * 2 ** 20
+REAL = {"f64": 8, "f32": 4, "f16": 2}
+HOP_FLOPS = 1320
+QTM_FLOPS = 2 * HOP_FLOPS + 72 + 96
+# FP64 ALU peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# DRAM bytes (read + write) per launch of Q_tm's launch B from ncu captures
+# (profiles/k_hop_f64_24x24x24x48_full.md, profiles/k_hop_dram_f32_f16_32x32x32x64.md),
+# scaled to a 32^3x64 launch by the site count, valid only for the kernel
+# sources they were taken from (hash of csrc/tm_device.cuh + csrc/tm_kernels.cu).
+TRAFFIC = {"src": "5162b3846366947c",
+           "per_site": {("f64", 18): (513.5e6 + 37.4e6) / 331776, ("f32", 12): (607.6e6 + 68.7e6) / 1048576,
+                        ("f16", 12): (312.1e6 + 27.7e6) / 1048576}}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("tm_device.cuh", "tm_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1311_4521_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(prec: str, recon: int, vh: int):
+    per = TRAFFIC["per_site"].get((prec, recon))
+    if per is None or kernel_source_hash() != TRAFFIC["src"]:
+        return None
+    return round(per * vh)
+
+
+def hop_bytes(prec: str, recon: int) -> int:
+    """Algorithmic bytes of one hop per output site: in spinor, out spinor, 8 links."""
+    b = (24 + 24 + 8 * recon) * REAL[prec]
+    return b + (8 if prec == "f16" else 0)           # per-site norms of the f16 spinors
+
+
+def algo_bytes(prec: str, recon: int) -> dict:
+    reread = 24 * REAL[prec] + (4 if prec == "f16" else 0)
+    a = hop_bytes(prec, recon)
+    b = hop_bytes(prec, recon) + reread
+    return {"kernel_a": a, "kernel_b": b, "qtm": a + b}
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(", ") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        if self.uuid:
+            mine = [r for r in rows if len(r) > 1 and self.uuid in r[1]]
+            rows = mine or rows
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 10:
+                continue
+            try:
+                sm.append(float(r[2].split()[0]))
+                smax.append(float(r[3].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[6:10]):
+                if v.strip() == "Active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def time_qtm(ctx, tmhop, torch, g, src, dst, steps: int, warmup: int, dist_barrier):
+    """Times `steps` Q_tm applications; per-launch CUDA events on the launching stream."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.Qtm(g, dst, src, KAPPA, MU)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for trio in ev:          # torch creates the CUDA event on first record
+        for e in trio:
+            e.record(stream)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist_barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(steps):
+        tmhop.tm_ctx_trace(ctx.handle, ev[k])
+        ctx.Qtm(g, dst, src, KAPPA, MU)
+    tmhop.tm_ctx_trace(ctx.handle, None)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier()
+    total_ms = t0.elapsed_time(t1)
+    ka = [e[0].elapsed_time(e[1]) for e in ev]
+    kb = [e[1].elapsed_time(e[2]) for e in ev]
+    return total_ms, float(np.mean(ka)), float(np.mean(kb))
+
+
+def gpu_arm(args) -> None:
+    import torch
+    from paper_1311_4521_gb300 import fields as F
+    from paper_1311_4521_gb300 import tmhop
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    DIMS = args.lattice
+    prec, recon = args.prec, args.recon
+    vh = int(np.prod(DIMS)) // 2
+    U = F.gauge_field(DIMS, F.SEED_PROD_32, "near", 0.3)
+    psi = F.gaussian_spinor(vh, F.SEED_PROD_32, 1)
+    ctx = tmhop.Context(local)
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "") or "") or None
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+
+    # ---- headline: FP64 storage, 18-real links (by default)
+    g = ctx.gauge(DIMS, U, prec, recon)
+    src = ctx.pack(psi, prec)
+    dst = ctx.empty(vh, prec)
+    clocks = ClockSampler(uuid).start()
+    total_ms, ka_ms, kb_ms = time_qtm(ctx, tmhop, torch, g, src, dst, args.steps, args.warmup, barrier)
+    ck = clocks.stop()
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(ck["reasons"]):
+        clocks = ClockSampler(uuid).start()
+        total_ms, ka_ms, kb_ms = time_qtm(ctx, tmhop, torch, g, src, dst, args.steps, args.warmup, barrier)
+        ck = clocks.stop()
+        ck["remeasured"] = True
+    max_ms = allmax(total_ms)
+    ab = algo_bytes(prec, recon)
+    ms_per_step = max_ms / args.steps
+    value = world * vh * ab["qtm"] / (ms_per_step * 1e-3) / 1e9
+    gflops = world * vh * QTM_FLOPS / (ms_per_step * 1e-3) / 1e9
+    kb_tflops = vh * (HOP_FLOPS + 96) / (kb_ms * 1e-3) / 1e12
+    kb_gbs = vh * ab["kernel_b"] / (kb_ms * 1e-3) / 1e9
+    traffic = args.traffic if args.traffic is not None else traffic_per_launch(prec, recon, vh)
+    kname = f"k_hop<{prec.upper()},{recon},HASX> (Q_tm second launch: H_eo + gamma5 twisted update)"
+    if prec == "f64":
+        roofline = {"bound": "alu", "achieved": round(kb_tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(kb_tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "kernel": kname,
+                    "peak_source": "FP64 FMA units: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.257)",
+                    "hbm_achieved_gbs": round(kb_gbs, 1), "hbm_frac": round(kb_gbs / hbm_peak, 4)}
+    else:
+        roofline = {"bound": "hbm", "achieved": round(kb_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(kb_gbs / hbm_peak, 4), "traffic": traffic, "kernel": kname,
+                    "peak_source": f"{hbm_src} HBM copy bandwidth"}
+    roofline.update({"kernel_a_ms": round(ka_ms, 4), "kernel_b_ms": round(kb_ms, 4),
+                     "bytes_per_launch": vh * ab["kernel_b"], "flops_per_launch": vh * (HOP_FLOPS + 96)})
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies in the timed region
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(np.ascontiguousarray(psi)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        dev_can = torch.empty(host_in.shape, dtype=torch.complex128, device="cuda")
+        dev_out = torch.empty_like(dev_can)
+        ne = max(1, min(args.steps, args.e2e_steps))
+
+        def e2e_step():
+            dev_can.copy_(host_in, non_blocking=True)
+            tmhop.tm_spinor_pack(ctx.handle, vh, torch.view_as_real(dev_can), src, tmhop.PREC[prec])
+            ctx.Qtm(g, dst, src, KAPPA, MU)
+            tmhop.tm_spinor_unpack(ctx.handle, vh, dst, torch.view_as_real(dev_out), tmhop.PREC[prec])
+            host_out.copy_(dev_out, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        s0.record()
+        for _ in range(ne):
+            e2e_step()
+        s1.record()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = allmax(s0.elapsed_time(s1)) / ne
+        nbytes = host_in.numel() * 16
+        e2e = {"value": round(world * vh * ab["qtm"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e2e_ms, 4),
+               "steps": ne, "gpu_launches_per_step": 4}
+        del host_in, host_out, dev_can, dev_out
+    links_gb = tmhop.tm_gauge_bytes(g.handle) / 1e9
+    g.close()
+
+    # ---- storage-precision table (HBM-bound variants)
+    table = {}
+    if not args.no_table:
+        for tp, tr in (("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12)):
+            gp = ctx.gauge(DIMS, U, tp, tr)
+            sp = ctx.pack(psi, tp)
+            dp = ctx.empty(vh, tp)
+            n = max(1, min(args.steps, args.table_steps))
+            t_ms, a_ms, b_ms = time_qtm(ctx, tmhop, torch, gp, sp, dp, n, args.warmup, barrier)
+            abp = algo_bytes(tp, tr)
+            step_ms = allmax(t_ms) / n
+            bgbs = vh * abp["kernel_b"] / (b_ms * 1e-3) / 1e9
+            table[f"{tp}-{tr}"] = {
+                "ms_per_qtm": round(step_ms, 4), "GBps": round(vh * abp["qtm"] / (step_ms * 1e-3) / 1e9, 1),
+                "gflops": round(vh * QTM_FLOPS / (step_ms * 1e-3) / 1e9, 1),
+                "kernel_b_ms": round(b_ms, 4), "kernel_b_GBps": round(bgbs, 1),
+                "kernel_b_hbm_frac": round(bgbs / hbm_peak, 4), "kernel_a_ms": round(a_ms, 4)}
+            gp.close()
+            del sp, dp
+
+    # ---- CPU baseline: the FP64 oracle on this host's cores, same lattice
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle as O
+        O.build()
+        t = time.perf_counter()
+        n = 0
+        while True:
+            O.Qtm(DIMS, U, psi, KAPPA, MU)
+            n += 1
+            if time.perf_counter() - t > args.cpu_seconds or n >= 8:
+                break
+        dt = (time.perf_counter() - t) / n
+        lat = "x".join(str(d) for d in DIMS)
+        cpu = {"value": round(vh * ab["qtm"] / dt / 1e9, 3), "unit": "GB/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+               "kind": "oracle", "sample": f"{n} full Q_tm applications on {lat} (FP64, OpenMP over sites)",
+               "s_per_qtm": round(dt, 3), "gflops": round(vh * QTM_FLOPS / dt / 1e9, 3)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
+            "config": {"workload": f"Q_tm, {'x'.join(str(d) for d in DIMS)}, {prec} storage, {recon}-real links, "
+                                   "U=exp(0.3iA), kappa=0.1394, mu=0.0015, antiperiodic t",
+                       "lattice": list(DIMS), "even_sites": vh, "storage": prec, "reconstruct": recon,
+                       "bytes_per_step": vh * ab["qtm"], "flops_per_step": vh * QTM_FLOPS,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 ({links_gb:.2f} GB links "
+                             f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"},
+            "gflops": round(gflops, 2), "roofline": roofline, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+def reference_arm(args) -> None:
+    """The FP64 CPU oracle as the reference implementation: each step is one
+    Q_tm on a 16^4 sample lattice of the same link distribution, on this
+    host's cores."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle as O
+    from paper_1311_4521_gb300 import fields as F
+    O.build()
+    vh = int(np.prod(SAMPLE_DIMS)) // 2
+    U = F.gauge_field(SAMPLE_DIMS, F.SEED_PROD_32, "near", 0.3)
+    psi = F.gaussian_spinor(vh, F.SEED_PROD_32, 1)
+    for _ in range(args.warmup):
+        O.Qtm(SAMPLE_DIMS, U, psi, KAPPA, MU)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        O.Qtm(SAMPLE_DIMS, U, psi, KAPPA, MU)
+    dt = (time.perf_counter() - t) / args.steps
+    ab = algo_bytes("f64", 18)
+    value = vh * ab["qtm"] / dt / 1e9
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    sample = f"one Q_tm per step on a 16^4 lattice (same link distribution, kappa, mu; FP64)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Q_tm, FP64, 18-real links, U=exp(0.3iA), kappa=0.1394, mu=0.0015 "
+                               "(16^4 sample of the 32^3x64 workload)", "lattice": list(SAMPLE_DIMS)},
+        "gflops": round(vh * QTM_FLOPS / dt / 1e9, 3),
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=DIMS,
+                    help="Lx,Ly,Lz,Lt (default 32,32,32,64)")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64")
+    ap.add_argument("--recon", type=int, choices=[12, 18], default=18)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--table-steps", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture of this build")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-table", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -3,7 +3,7 @@
  * preconditioned Wilson twisted-mass operator.
  *
  * The operator is the one whose hopping matrix the tmLQCD suite optimises
- * (arXiv:1311.4521, Sec. 1-2: "Hopping_Matrix", full- and half-spinor
+ * (arXiv:1311.4521, introduction and Sec. 2: "Hopping_Matrix", full- and half-spinor
  * kernels, "Dirac matrix inversion" by the inverter), in the standard
  * hopping-parameter form:
  *
@@ -71,6 +71,14 @@ void tm_ctx_destroy(tm_ctx *ctx);
 /* Message of the last failure on ctx (never NULL; "" if none). */
 const char *tm_last_error(const tm_ctx *ctx);
 const char *tm_status_string(tm_status s);
+/* Tracing hook for timing individual kernels with CUDA events.  While
+ * events != NULL, each later multi-kernel call records events[k] (cudaEvent_t
+ * values created by the caller) on its stream at its kernel boundaries:
+ * tm_Qtm records events[0] before its first launch, events[1] between its
+ * two launches and events[2] after the second.  nevents must be >= 3.
+ * Pass events = NULL to stop.  The array is copied; the events are not
+ * owned by the library. */
+tm_status tm_ctx_trace(tm_ctx *ctx, void *const *events, int nevents);
 
 /* ---- fields --------------------------------------------------------------- */
 
@@ -107,10 +115,11 @@ size_t tm_gauge_bytes(const tm_gauge *g);
 /* ---- operator ------------------------------------------------------------ */
 
 /* out = H psi for dir TM_EO (H_eo: odd in, even out) or TM_OE (H_oe: even
- * in, odd out); dagger != 0 applies H^dagger instead, i.e. the hop with
- * both spin projectors swapped (gamma5 H gamma5 of the opposite direction).
- * Fields are packed in the gauge handle's precision; out and in must not
- * overlap. */
+ * in, odd out).  dagger != 0 applies the adjoint hop Dhop^dagger between
+ * the same parities instead: for TM_EO that is H_oe^dagger = gamma5 H_eo
+ * gamma5, the hop with its two spin projectors (1 -+ gamma_mu) swapped;
+ * for TM_OE it is H_eo^dagger.  Fields are packed in the gauge handle's
+ * precision; out and in must not overlap. */
 tm_status tm_hopping_eo(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const void *in_dev, int dir, int dagger,
                         void *stream);
 

@@ -35,7 +35,6 @@ bool valid_prec(int p) { return p == TM_F64 || p == TM_F32 || p == TM_F16; }
 
 }  // namespace
 
-// Grows the context's scratch buffer to at least `bytes` (16-byte aligned slices are carved from it).
 tm_status tm_ctx_scratch(tm_ctx *ctx, size_t bytes, void **ptr)
 {
     if (ctx->scratch_bytes < bytes) {
@@ -90,6 +89,22 @@ void tm_ctx_destroy(tm_ctx *ctx)
 }
 
 const char *tm_last_error(const tm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+tm_status tm_ctx_trace(tm_ctx *ctx, void *const *events, int nevents)
+{
+    if (!ctx) return TM_ERR_ARG;
+    ctx->trace.clear();
+    if (!events) return TM_OK;
+    if (nevents < 3) return fail(ctx, TM_ERR_ARG, "tm_ctx_trace: need at least 3 events");
+    for (int k = 0; k < nevents; ++k) {
+        if (!events[k]) {
+            ctx->trace.clear();
+            return fail(ctx, TM_ERR_ARG, "tm_ctx_trace: null event");
+        }
+        ctx->trace.push_back(static_cast<cudaEvent_t>(events[k]));
+    }
+    return TM_OK;
+}
 
 size_t tm_spinor_bytes(long vh, int prec)
 {
@@ -188,10 +203,13 @@ tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in
     if (st != TM_OK) return st;
     double mut = 2.0 * kappa * mu * sign;
     cudaStream_t s = (cudaStream_t)stream;
+    tm_trace_mark(ctx, 0, s);
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, in_e_dev, tmp, nullptr,
                             coef_qtm_a(mut), s, 128));
+    tm_trace_mark(ctx, 1, s);
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, tmp, out_e_dev, in_e_dev,
                             coef_qtm_b(kappa, mut), s, 128));
+    tm_trace_mark(ctx, 2, s);
     return TM_OK;
 }
 

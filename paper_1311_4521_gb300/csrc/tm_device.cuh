@@ -8,7 +8,8 @@
 // instead of being read from the g_iup/g_idn/g_hi tables of Sec. 2.2, so
 // index lookups cost no memory traffic at all.
 //
-// The spin structure uses the half-spinor ("Weyl-type") form of Sec. 1:
+// The spin structure uses the half-spinor ("Weyl-type") form that the
+// paper's introduction names for tmLQCD's Hopping_Matrix:
 // in the chiral basis gamma_mu = [[0, A_mu], [A_mu^dag, 0]] with A_0 = -1,
 // A_k = -i sigma_k, and
 //     (1 + s gamma_mu) psi = ( h , s A_mu^dag h ),   h = u + s A_mu l,

@@ -16,7 +16,17 @@ struct tm_ctx {
     void *scratch = nullptr;       // odd-parity temporaries of Q_tm and friends
     size_t scratch_bytes = 0;
     int sm_count = 0;
+    std::vector<cudaEvent_t> trace;  // events recorded at kernel boundaries (tm_ctx_trace)
 };
+
+// Records trace event k of ctx on stream s, if tracing is on.
+inline void tm_trace_mark(tm_ctx *ctx, size_t k, cudaStream_t s)
+{
+    if (k < ctx->trace.size()) cudaEventRecord(ctx->trace[k], s);
+}
+
+// Grows the context's scratch buffer to at least `bytes` and returns it.
+tm_status tm_ctx_scratch(tm_ctx *ctx, size_t bytes, void **ptr);
 
 struct tm_gauge {
     tm_ctx *ctx = nullptr;

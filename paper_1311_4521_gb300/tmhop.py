@@ -43,6 +43,7 @@ def _load() -> ctypes.CDLL:
         "tm_ctx_destroy": ([P], None),
         "tm_last_error": ([P], ctypes.c_char_p),
         "tm_status_string": ([I], ctypes.c_char_p),
+        "tm_ctx_trace": ([P, P, I], I),
         "tm_spinor_bytes": ([L, I], S),
         "tm_spinor_pack": ([P, L, P, P, I, P], I),
         "tm_spinor_unpack": ([P, L, P, P, I, P], I),
@@ -103,6 +104,15 @@ def tm_last_error(ctx) -> str:
 
 def tm_status_string(status: int) -> str:
     return lib.tm_status_string(int(status)).decode()
+
+
+def tm_ctx_trace(ctx, events) -> None:
+    """Records the given torch.cuda.Event objects at kernel boundaries (None stops)."""
+    if events is None:
+        _check(ctx, lib.tm_ctx_trace(ctx, None, 0))
+        return
+    arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+    _check(ctx, lib.tm_ctx_trace(ctx, arr, len(events)))
 
 
 def tm_spinor_bytes(vh: int, prec: int) -> int:
