@@ -131,6 +131,30 @@ tm_status tm_hopping_eo(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const voi
 tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in_e_dev, double kappa, double mu,
                  int sign, void *stream);
 
+/* Size in bytes of the static device array behind tm_Qtm_noalloc: room for
+ * one odd-parity field of up to 174,762 sites in TM_F64 (e.g. 24^3x24),
+ * 349,525 in TM_F32 (24^3x48) or 645,277 in TM_F16 (32^3x32 and below).
+ * Every GPU that loads this library holds it until the process exits. */
+#define TM_QTM_NOALLOC_MAX_BYTES (32u << 20)
+
+/* Same operator and arguments as tm_Qtm, for callers that cannot let the
+ * library allocate device memory (a framework that owns all device memory
+ * through its own pool, a plugin with a fixed memory budget, a loop that
+ * cannot take the device synchronisation an allocation may cause).  The
+ * paper has no counterpart; this is an interface addition.  The odd
+ * temporary lives in a static device array of TM_QTM_NOALLOC_MAX_BYTES
+ * bytes instead of the context's scratch buffer, and the call makes no
+ * cudaMalloc or cudaFree.  The gauge handle and the fields are still the
+ * caller's, created beforehand.  Lattices whose odd temporary
+ * (tm_spinor_bytes(V/2, prec)) exceeds the array are rejected with
+ * TM_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device made current for the
+ * lookup); make that first call before any stream capture.  All calls on a
+ * device share the one array, which keeps the last call's contents; calls
+ * that overlap on the GPU race on it. */
+tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in_e_dev, double kappa,
+                         double mu, int sign, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

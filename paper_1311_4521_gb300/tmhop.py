@@ -52,6 +52,7 @@ def _load() -> ctypes.CDLL:
         "tm_gauge_bytes": ([P], S),
         "tm_hopping_eo": ([P, P, P, P, I, I, P], I),
         "tm_Qtm": ([P, P, P, P, D, D, I, P], I),
+        "tm_Qtm_noalloc": ([P, P, P, P, D, D, I, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -149,6 +150,15 @@ def tm_hopping_eo(ctx, U, out_dev, in_dev, dir, dagger=0, stream=None):
 def tm_Qtm(ctx, U, out_e_dev, in_e_dev, kappa, mu, sign=1, stream=None):
     _check(ctx, lib.tm_Qtm(ctx, U, _ptr(out_e_dev), _ptr(in_e_dev), float(kappa), float(mu), int(sign),
                            _stream(stream)))
+
+
+def tm_Qtm_noalloc(ctx, U, out_e_dev, in_e_dev, kappa, mu, sign=1, stream=None):
+    """tm_Qtm with its temporary in the library's static device array: no device allocation."""
+    _check(ctx, lib.tm_Qtm_noalloc(ctx, U, _ptr(out_e_dev), _ptr(in_e_dev), float(kappa), float(mu), int(sign),
+                                   _stream(stream)))
+
+
+TM_QTM_NOALLOC_MAX_BYTES = 32 << 20
 
 
 # ---- convenience layer over torch tensors -----------------------------------------
