@@ -309,6 +309,11 @@ def gpu_arm(args) -> None:
             gp.close()
             del sp, dp
 
+    # ---- CG on Q^dag Q to true relative residual 1e-10: FP64 vs mixed precision
+    cg = None
+    if not args.no_cg:
+        cg = cg_section(args, ctx, tmhop, torch, F, allmax, barrier)
+
     # ---- CPU baseline: the FP64 oracle on this host's cores, same lattice
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -340,13 +345,51 @@ def gpu_arm(args) -> None:
                        "l2": f"inputs larger than L2 ({links_gb:.2f} GB links "
                              f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"},
             "gflops": round(gflops, 2), "roofline": roofline, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "cg": cg,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def cg_section(args, ctx, tmhop, torch, F, allmax, barrier) -> dict:
+    """Time to a true relative residual of 1e-10 for Q^dag Q x = b on the CG
+    lattice (48^3x96 by default, U = exp(0.3 i A), Gaussian source): plain
+    FP64 CG against mixed precision with FP32 and FP16 storage (FP32
+    arithmetic, FP64 reliable updates).  Each solver runs once to warm up,
+    then once timed with CUDA events around the (synchronous) call."""
+    dims = args.cg_lattice
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, F.SEED_CG_48, "near", 0.3)
+    b = F.gaussian_spinor(vh, F.SEED_CG_48, 1)
+    gh = ctx.gauge(dims, U, "f64", 18)
+    lo = {"mixed_f32": ctx.gauge(dims, U, "f32", 12), "mixed_f16": ctx.gauge(dims, U, "f16", 12)}
+    del U
+    bd = ctx.pack(b, "f64")
+    x = ctx.empty(vh, "f64")
+    out = {"lattice": list(dims), "tol": 1e-10, "kappa": KAPPA, "mu": MU, "reliable_every": 50,
+           "reliable_delta": 0.1, "source": "Gaussian, seed 2013", "time": "CUDA events around one warm solve"}
+    stream = torch.cuda.current_stream()
+    for name, gl in (("fp64", None), ("mixed_f32", lo["mixed_f32"]), ("mixed_f16", lo["mixed_f16"])):
+        for rep in range(2):
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st, info = ctx.cg(gh, x, bd, KAPPA, MU, 1e-10, 30000, gl, 50, True, 0.1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        sec = allmax(e0.elapsed_time(e1) / 1e3)
+        out[name] = {"seconds": round(sec, 4), "iters": info["iters"], "reliable_updates": info["reliable_updates"],
+                     "true_relres": info["true_relres"], "converged": st == tmhop.TM_OK}
+    for name in ("mixed_f32", "mixed_f16"):
+        out[name]["speedup_vs_fp64"] = round(out["fp64"]["seconds"] / out[name]["seconds"], 2)
+    for g in [gh] + list(lo.values()):
+        g.close()
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
@@ -402,6 +445,8 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--cg-lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=(48, 48, 48, 96))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))

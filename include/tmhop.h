@@ -131,6 +131,52 @@ tm_status tm_hopping_eo(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const voi
 tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in_e_dev, double kappa, double mu,
                  int sign, void *stream);
 
+/* ---- solver ------------------------------------------------------------- */
+
+/* Parameters of tm_cg_QdagQ. */
+typedef struct {
+    double kappa, mu;      /* operator parameters of Q_tm (mu is the twisted mass, mut = 2 kappa mu) */
+    double tol;            /* target true relative residual |b - Q^dag Q x|_2 / |b|_2, checked in FP64 */
+    int maxiter;           /* iteration limit (counted in inner CG iterations) */
+    int reliable_every;    /* iterations per segment between host checks; with a reduced-precision
+                              inner solver also the longest stretch without a reliable update */
+    int use_graph;         /* nonzero: capture one segment as a CUDA graph and replay it */
+    double reliable_delta; /* reduced-precision inner solver: FP64 reliable update (x += y,
+                              r = b - Q^dag Q x in FP64) as soon as the recursive |r| has fallen
+                              below reliable_delta times its largest value since the previous
+                              one (0 <= delta < 1; 0: only every reliable_every iterations) */
+} tm_cg_params;
+
+/* Results of tm_cg_QdagQ. */
+typedef struct {
+    int iters;             /* inner CG iterations performed */
+    int reliable_updates;  /* FP64 residual recomputations (reliable updates and final checks) */
+    double true_relres;    /* final |b - Q^dag Q x| / |b| computed in FP64 */
+    double seconds;        /* wall time of the solve, host clock, from entry to the final synchronisation */
+    int status;            /* tm_status of the solve */
+} tm_cg_info;
+
+/* Solves Q^dag Q x = b on the even sites by conjugate gradients, the
+ * inversion the tmLQCD inverter performs (the paper's Sec. 3 samples it;
+ * Q^dag Q = Q(-mu) Q(mu) is Hermitian positive definite for mu != 0).
+ *
+ * U_hi is an FP64 gauge handle; x_dev (in: initial guess, out: solution)
+ * and b_dev are FP64 packed even fields.  U_lo selects the inner solver:
+ * NULL or U_hi gives a plain FP64 CG, checked against the FP64 true
+ * residual whenever the recursive residual reaches tol; an FP32 or FP16
+ * handle gives a mixed-precision CG whose vectors are stored in that
+ * precision with FP32 arithmetic; its solution increments are accumulated
+ * (in FP32) and added to x in FP64 at each reliable update, where the
+ * residual is recomputed in FP64 and replaces the recursive one (the
+ * search direction is kept).  Inner products are reduced in FP64, in a fixed order
+ * (bit-reproducible).  Convergence is declared only on the FP64 true
+ * residual.  Returns TM_OK, TM_ERR_NOT_CONVERGED (x holds the last iterate)
+ * or TM_ERR_NONFINITE; info (may be NULL) receives the statistics.
+ * Synchronous: returns after the solve has finished on `stream`.  Scratch
+ * fields are owned by ctx. */
+tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gauge *U_lo, void *x_dev, const void *b_dev,
+                      const tm_cg_params *params, tm_cg_info *info, void *stream);
+
 /* Size in bytes of the static device array behind tm_Qtm_noalloc: room for
  * one odd-parity field of up to 174,762 sites in TM_F64 (e.g. 24^3x24),
  * 349,525 in TM_F32 (24^3x48) or 645,277 in TM_F16 (32^3x32 and below).

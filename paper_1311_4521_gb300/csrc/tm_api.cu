@@ -85,6 +85,7 @@ void tm_ctx_destroy(tm_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->ws) cudaFree(ctx->ws);
     delete ctx;
 }
 

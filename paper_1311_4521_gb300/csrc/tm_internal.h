@@ -17,6 +17,8 @@ struct tm_ctx {
     size_t scratch_bytes = 0;
     int sm_count = 0;
     std::vector<cudaEvent_t> trace;  // events recorded at kernel boundaries (tm_ctx_trace)
+    void *ws = nullptr;              // solver workspace (grow-only)
+    size_t ws_bytes = 0;
 };
 
 // Records trace event k of ctx on stream s, if tracing is on.
@@ -27,6 +29,8 @@ inline void tm_trace_mark(tm_ctx *ctx, size_t k, cudaStream_t s)
 
 // Grows the context's scratch buffer to at least `bytes` and returns it.
 tm_status tm_ctx_scratch(tm_ctx *ctx, size_t bytes, void **ptr);
+// Grows the context's solver workspace to at least `bytes` and returns it.
+tm_status tm_ctx_workspace(tm_ctx *ctx, size_t bytes, void **ptr);
 
 struct tm_gauge {
     tm_ctx *ctx = nullptr;

@@ -28,12 +28,32 @@ spectra and fully random ones for small correctness cases.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 _G = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
-_CHUNK = 1 << 20
+_CHUNK = 1 << 18
+_THREADS = max(1, min(32, os.cpu_count() or 1))
+
+
+def _chunked(n: int, fill) -> None:
+    """Calls fill(lo, m) for consecutive chunks of [0, n) on a thread pool.
+
+    Every draw is addressed by its counter, so the result does not depend
+    on the chunking or on the order in which chunks run; numpy releases the
+    GIL inside its array operations, so chunks run in parallel.
+    """
+    spans = [(lo, min(_CHUNK, n - lo)) for lo in range(0, n, _CHUNK)]
+    if len(spans) <= 1 or _THREADS == 1:
+        for lo, m in spans:
+            fill(lo, m)
+        return
+    with ThreadPoolExecutor(_THREADS) as ex:
+        list(ex.map(lambda a: fill(*a), spans))
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -98,10 +118,12 @@ def random_su3(n: int, seed: int, field: int) -> np.ndarray:
     """``n`` Haar-like random SU(3) matrices, shape (n, 3, 3)."""
     s = stream_seed(seed, field)
     out = np.empty((n, 3, 3), dtype=np.complex128)
-    for lo in range(0, n, _CHUNK):
-        m = min(_CHUNK, n - lo)
+
+    def fill(lo, m):
         z = _complex_normals(s, 6 * lo, 6 * m).reshape(m, 2, 3)
         out[lo:lo + m] = _orthonormal_rows(z[:, 0], z[:, 1])
+
+    _chunked(n, fill)
     return out
 
 
@@ -118,21 +140,32 @@ _LAMBDA[7][0, 0] = _LAMBDA[7][1, 1] = 1 / np.sqrt(3)
 _LAMBDA[7][2, 2] = -2 / np.sqrt(3)
 
 
-def _expm_small(X: np.ndarray) -> np.ndarray:
-    """exp(X) for a batch of small 3x3 matrices, shape (n, 3, 3).
+def _expm_traceless(X: np.ndarray, terms: int = 24) -> np.ndarray:
+    """exp(X) for a batch of traceless 3x3 matrices, shape (n, 3, 3).
 
-    Scaling and squaring with a truncated Taylor series: X is divided by 2^4,
-    the series is summed to order 14 (remainder below 1e-25 for ||X|| < 4),
-    and the result is squared four times.
+    By Cayley-Hamilton a traceless 3x3 matrix obeys X^3 = -c X + d 1 with
+    c = -tr(X^2)/2 and d = det X, so every power X^k/k! is a_k 1 + b_k X +
+    c_k X^2 and the Taylor series reduces to a scalar recurrence on
+    (a_k, b_k, c_k).  For ||X|| <= 1.5 the remainder after 24 terms is
+    below 1e-20.
     """
-    Y = X / 16.0
-    n = X.shape[0]
-    eye = np.broadcast_to(np.eye(3, dtype=np.complex128), (n, 3, 3))
-    E = eye.copy()
-    for k in range(14, 0, -1):
-        E = eye + np.matmul(Y, E) / k
-    for _ in range(4):
-        E = np.matmul(E, E)
+    X2 = np.matmul(X, X)
+    c = -0.5 * (X2[:, 0, 0] + X2[:, 1, 1] + X2[:, 2, 2])
+    d = (X[:, 0, 0] * (X[:, 1, 1] * X[:, 2, 2] - X[:, 1, 2] * X[:, 2, 1])
+         - X[:, 0, 1] * (X[:, 1, 0] * X[:, 2, 2] - X[:, 1, 2] * X[:, 2, 0])
+         + X[:, 0, 2] * (X[:, 1, 0] * X[:, 2, 1] - X[:, 1, 1] * X[:, 2, 0]))
+    a = np.ones_like(c)
+    b = np.zeros_like(c)
+    q = np.zeros_like(c)
+    fa, fb, fq = a.copy(), b.copy(), q.copy()
+    for k in range(1, terms + 1):
+        a, b, q = q * d / k, (a - q * c) / k, b / k
+        fa += a
+        fb += b
+        fq += q
+    E = fb[:, None, None] * X + fq[:, None, None] * X2
+    for i in range(3):
+        E[:, i, i] += fa
     return E
 
 
@@ -140,12 +173,14 @@ def near_identity_su3(n: int, seed: int, field: int, eps: float = 0.3) -> np.nda
     """``n`` matrices exp(i*eps*A), A = sum_a w_a lambda_a/2, re-unitarised to SU(3)."""
     s = stream_seed(seed, field)
     out = np.empty((n, 3, 3), dtype=np.complex128)
-    for lo in range(0, n, _CHUNK):
-        m = min(_CHUNK, n - lo)
+
+    def fill(lo, m):
         w = normal(s, 4 * lo, 8 * m).reshape(m, 8)
         A = np.einsum("na,aij->nij", w, _LAMBDA) * 0.5
-        U = _expm_small(1j * eps * A)
+        U = _expm_traceless(1j * eps * A)
         out[lo:lo + m] = _orthonormal_rows(U[:, 0], U[:, 1])
+
+    _chunked(n, fill)
     return out
 
 
@@ -175,9 +210,11 @@ def gaussian_spinor(n: int, seed: int, field: int) -> np.ndarray:
     """``n`` spinors with i.i.d. complex Gaussian components, shape (n, 4, 3)."""
     s = stream_seed(seed, field)
     out = np.empty(n * 12, dtype=np.complex128)
-    for lo in range(0, n * 12, 12 * _CHUNK):
-        m = min(12 * _CHUNK, n * 12 - lo)
+
+    def fill(lo, m):
         out[lo:lo + m] = _complex_normals(s, lo, m)
+
+    _chunked(n * 12, fill)
     return out.reshape(n, 4, 3)
 
 

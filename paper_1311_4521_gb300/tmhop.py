@@ -25,6 +25,22 @@ TM_EO, TM_OE = 0, 1
 PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16}
 
 
+class CgParams(ctypes.Structure):
+    """tm_cg_params."""
+    _fields_ = [("kappa", ctypes.c_double), ("mu", ctypes.c_double), ("tol", ctypes.c_double),
+                ("maxiter", ctypes.c_int), ("reliable_every", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reliable_delta", ctypes.c_double)]
+
+
+class CgInfo(ctypes.Structure):
+    """tm_cg_info."""
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_relres", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class TmError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"[{status}] {message}")
@@ -53,6 +69,7 @@ def _load() -> ctypes.CDLL:
         "tm_hopping_eo": ([P, P, P, P, I, I, P], I),
         "tm_Qtm": ([P, P, P, P, D, D, I, P], I),
         "tm_Qtm_noalloc": ([P, P, P, P, D, D, I, P], I),
+        "tm_cg_QdagQ": ([P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -152,6 +169,17 @@ def tm_Qtm(ctx, U, out_e_dev, in_e_dev, kappa, mu, sign=1, stream=None):
                            _stream(stream)))
 
 
+def tm_cg_QdagQ(ctx, U_hi, U_lo, x_dev, b_dev, params: CgParams, stream=None):
+    """Runs the solver; returns (status, CgInfo).  Raises TmError for argument and CUDA errors only:
+    TM_ERR_NOT_CONVERGED and TM_ERR_NONFINITE come back as the status."""
+    info = CgInfo()
+    st = lib.tm_cg_QdagQ(ctx, U_hi, U_lo, _ptr(x_dev), _ptr(b_dev), ctypes.byref(params), ctypes.byref(info),
+                         _stream(stream))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE):
+        _check(ctx, st)
+    return st, info
+
+
 def tm_Qtm_noalloc(ctx, U, out_e_dev, in_e_dev, kappa, mu, sign=1, stream=None):
     """tm_Qtm with its temporary in the library's static device array: no device allocation."""
     _check(ctx, lib.tm_Qtm_noalloc(ctx, U, _ptr(out_e_dev), _ptr(in_e_dev), float(kappa), float(mu), int(sign),
@@ -249,3 +277,11 @@ class Context:
     def Qtm(self, U: Gauge, out, inp, kappa, mu, sign=1):
         tm_Qtm(self.handle, U.handle, out, inp, kappa, mu, sign)
         return out
+
+    def cg(self, U_hi: Gauge, x, b, kappa, mu, tol=1e-10, maxiter=30000, U_lo: Gauge | None = None,
+           reliable_every=50, use_graph=True, reliable_delta=0.1):
+        """Solves Q^dag Q x = b (x: packed FP64 even field, in/out).  Returns (status, info dict)."""
+        prm = CgParams(float(kappa), float(mu), float(tol), int(maxiter), int(reliable_every), int(bool(use_graph)),
+                       float(reliable_delta))
+        st, info = tm_cg_QdagQ(self.handle, U_hi.handle, U_lo.handle if U_lo is not None else None, x, b, prm)
+        return st, info.as_dict()

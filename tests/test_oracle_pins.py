@@ -133,6 +133,17 @@ def test_generators_are_su3_and_deterministic():
     np.testing.assert_array_equal(a, b)
 
 
+def test_generator_exponential_matches_library_expm():
+    """The Cayley-Hamilton series of the link generator against scipy's expm."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    w = F.normal(F.stream_seed(9, 9), 0, 8 * 50).reshape(50, 8)
+    X = 1j * 0.3 * np.einsum("na,aij->nij", w, F._LAMBDA) * 0.5
+    X[0] *= 4.0   # a large-norm case
+    E = F._expm_traceless(X)
+    want = np.stack([scipy_linalg.expm(x) for x in X])
+    assert np.abs(E - want).max() < 1e-13
+
+
 def test_gamma_basis_clifford_and_chirality():
     g = O.gammas()
     for m in range(4):
