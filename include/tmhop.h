@@ -80,6 +80,12 @@ const char *tm_status_string(tm_status s);
  * owned by the library. */
 tm_status tm_ctx_trace(tm_ctx *ctx, void *const *events, int nevents);
 
+/* Turns timing-based selection of launch configurations on (default) or
+ * off.  With it on, the first batched call for a new batch shape runs a few
+ * candidate configurations of its hop launch and keeps the fastest for the
+ * context's lifetime; off, a fixed configuration is used. */
+tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on);
+
 /* ---- fields --------------------------------------------------------------- */
 
 /* Bytes of one packed one-parity spinor field of Vh sites in precision prec:
@@ -176,6 +182,32 @@ typedef struct {
  * fields are owned by ctx. */
 tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gauge *U_lo, void *x_dev, const void *b_dev,
                       const tm_cg_params *params, tm_cg_info *info, void *stream);
+
+/* ---- batches ------------------------------------------------------------ */
+
+/* Q_tm(sign*mu) applied to nsys even fields (out_e[k] = Q in_e[k] with gauge
+ * U[k]) with one launch per hop for the whole batch.  Systems that share a
+ * gauge handle pointer are several right-hand sides of one lattice: the
+ * links of each site are read once and applied to all of them.  Systems on
+ * different handles may have different lattice sizes.  All handles must
+ * have the same precision and reconstruction.  Scratch (odd temporaries)
+ * is owned by ctx.  Synchronous with respect to stream. */
+tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U, void *const *out_e, const void *const *in_e,
+                       double kappa, double mu, int sign, void *stream);
+
+/* Solves the nsys systems Q^dag Q x[k] = b[k] at once, each step of the
+ * iteration one launch over all of them (systems sharing U_hi[k] reuse its
+ * links as in tm_Qtm_batch).  U_hi[k] are FP64 handles; U_lo (may be NULL)
+ * gives each system's inner handle (NULL or U_lo[k] == U_hi[k]: FP64 inner
+ * solver); systems sharing U_hi need the same U_lo; all inner handles need
+ * the same precision.  Every system uses the reliable-update scheme of
+ * tm_cg_QdagQ with its own scalars and stops on its own FP64 true residual;
+ * params are shared.  info[k] receives system k's statistics (seconds is
+ * the batch's wall time).  Returns TM_OK if every system converged, else
+ * TM_ERR_NONFINITE or TM_ERR_NOT_CONVERGED. */
+tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U_hi, const tm_gauge *const *U_lo,
+                            void *const *x_dev, const void *const *b_dev, const tm_cg_params *params,
+                            tm_cg_info *info, void *stream);
 
 /* Size in bytes of the static device array behind tm_Qtm_noalloc: room for
  * one odd-parity field of up to 174,762 sites in TM_F64 (e.g. 24^3x24),

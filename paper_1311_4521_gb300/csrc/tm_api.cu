@@ -91,6 +91,13 @@ void tm_ctx_destroy(tm_ctx *ctx)
 
 const char *tm_last_error(const tm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on)
+{
+    if (!ctx) return TM_ERR_ARG;
+    ctx->autotune = on ? 1 : 0;
+    return TM_OK;
+}
+
 tm_status tm_ctx_trace(tm_ctx *ctx, void *const *events, int nevents)
 {
     if (!ctx) return TM_ERR_ARG;

@@ -1,0 +1,893 @@
+// tm_batch.cu -- the operator and the solver over many systems at once:
+// several right-hand sides on one lattice and several lattices of uneven
+// volume, each step of the iteration one launch over all of them.
+//
+// Systems that share a gauge handle form a group.  A launch walks a work
+// list of tiles of all groups; its CTAs are persistent (each takes items
+// blockIdx.x, blockIdx.x + gridDim.x, ...), so one launch covers every
+// lattice whatever their sizes.  For a group with several right-hand sides
+// the CTA copies the 8 links of each tile site into shared memory once and
+// applies them to all right-hand sides (the links are most of the bytes of
+// a hop, so n right-hand sides cost much less than n launches); with one
+// right-hand side per group links are read straight from global memory.
+// Tile size (right-hand sides processed together) and the number of
+// persistent CTAs are picked by timing candidates on first use.
+//
+// Every system keeps its own CG scalars; reductions write one partial per
+// (system, tile) and a small finishing launch sums them in index order.
+// Kernels of finished systems, and reliable-update stages not due, exit at
+// once, so a whole segment of iterations replays as one CUDA graph.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "tm_cg.cuh"
+#include "tm_internal.h"
+
+namespace twm {
+
+enum Role { R_X, R_B, R_R, R_P, R_AP, R_Q, R_T, R_Y, R_AX, R_THI, R_QHI, R_IN, R_OUT, NROLE };
+
+struct BSys {
+    void *f[NROLE];
+    double *partials;  // one slot per work tile of the system's lattice
+    CgScalars *s;
+    unsigned vh;
+};
+
+struct BGroup {
+    Geom g;
+    const void *links;  // gauge storage in the launch's precision
+    int nrhs, sys0;     // systems sys0 .. sys0 + nrhs - 1
+    unsigned item0;     // first work item of the group
+    unsigned ntiles;    // tiles covering the group's Vh sites
+};
+
+constexpr int BT = 128;   // threads per CTA of the batched hop
+constexpr int BLA = 256;  // threads per CTA of the batched vector kernels
+
+__device__ __forceinline__ int find_group(const BGroup *gr, int ng, unsigned item)
+{
+    int gi = 0;
+    while (gi + 1 < ng && item >= gr[gi + 1].item0) ++gi;
+    return gi;
+}
+
+template <int P, int RECON, int NRB, bool NORM>
+__global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ groups, int ngroups, unsigned nitems,
+                                                  const BSys *__restrict__ sys, int parity, int rin, int rout, int rx,
+                                                  Coef k, int gate)
+{
+    using L = LinkIO<P, RECON>;
+    using V = typename L::V;
+    using R = typename SpinorIO<P>::R;
+    constexpr int TS = BT / NRB;
+    __shared__ V tile[NRB > 1 ? 8 * L::NCHUNK * TS : 1];
+    __shared__ unsigned bwd_idx[NRB > 1 ? 4 * TS : 1];
+    __shared__ double red[BT];
+    const unsigned tx = threadIdx.x % TS, ty = threadIdx.x / TS;
+
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const BGroup &G = groups[find_group(groups, ngroups, item)];
+        const unsigned rel = item - G.item0;
+        const unsigned tno = NRB == 1 ? rel % G.ntiles : rel;
+        const unsigned i = tno * TS + tx;
+        const V *links = static_cast<const V *>(G.links);
+        if (NRB > 1) {
+            __syncthreads();  // readers of the previous tile are done
+            if (ty == 0) {
+                unsigned site = tno * TS + tx;
+                if (site < G.g.vh) {
+                    Nbrs n;
+                    neighbours(G.g, parity, site, n);
+                    for (int m = 0; m < 4; ++m) bwd_idx[m * TS + tx] = n.bwd[m];
+                }
+            }
+            __syncthreads();
+            for (unsigned e = threadIdx.x; e < 8u * L::NCHUNK * TS; e += BT) {
+                const unsigned s = e % TS, dc = e / TS, c = dc % L::NCHUNK, d = dc / L::NCHUNK;
+                const unsigned site = tno * TS + s;
+                V v{};
+                if (site < G.g.vh) {
+                    const unsigned idx = d < 4 ? site : bwd_idx[(d - 4) * TS + s];
+                    const unsigned blk = d < 4 ? 4 * parity + d : 4 * (1 - parity) + (d - 4);
+                    v = ld_stream(links + (size_t(blk) * L::NCHUNK + c) * G.g.vh + idx);
+                }
+                tile[e] = v;
+            }
+            __syncthreads();
+        }
+        const int passes = NRB == 1 ? 1 : (G.nrhs + NRB - 1) / NRB;
+        for (int q = 0; q < passes; ++q) {
+            const int r = NRB == 1 ? int(rel / G.ntiles) : q * NRB + int(ty);
+            const BSys *S = r < G.nrhs ? &sys[G.sys0 + r] : nullptr;
+            const bool active = S && !gated(S->s, gate);
+            double nrm = 0.0;
+            if (active && i < G.g.vh) {
+                Spinor<R> acc, o;
+                Nbrs n;
+                neighbours(G.g, parity, i, n);
+                if (NRB > 1) {
+                    StagedLinks<P, RECON> src{tile, TS, tx};
+                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
+                } else {
+                    GlobalLinks<P, RECON> src{links, G.g.vh, i, parity};
+                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
+                }
+                if (rx >= 0) {
+                    Spinor<R> xs;
+                    SpinorIO<P>::load(S->f[rx], G.g.vh, i, xs);
+                    epilogue(k, acc, &xs, o);
+                } else {
+                    epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
+                }
+                SpinorIO<P>::store(S->f[rout], G.g.vh, i, o);
+                if (NORM) nrm = norm2(o);
+            }
+            if (NORM) {
+                // one partial per (system, tile): the TS threads of each right-hand side, summed in order
+                red[threadIdx.x] = nrm;
+                __syncthreads();
+                if (tx == 0 && active) {
+                    double sum = 0.0;
+                    for (int t = 0; t < TS; ++t) sum += red[ty * TS + t];
+                    S->partials[tno] = sum;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// Maps a vector-kernel item to (system, tile of BLA sites) by the prefix table item0[nsys+1].
+__device__ __forceinline__ int find_sys(const unsigned *item0, int nsys, unsigned item)
+{
+    int k = 0;
+    while (k + 1 < nsys && item >= item0[k + 1]) ++k;
+    return k;
+}
+
+// Block sum of v over BLA threads in a fixed order; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = BLA / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < unsigned(w)) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// y += alpha p, r -= alpha Ap, partial |r|^2
+template <int P, int PY>
+__global__ void __launch_bounds__(BLA) k_batch_update(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+                                                      unsigned nitems, int gate)
+{
+    using R = typename SpinorIO<P>::R;
+    using RY = typename SpinorIO<PY>::R;
+    __shared__ double red[BLA];
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int k = find_sys(item0, nsys, item);
+        const BSys &S = sys[k];
+        if (gated(S.s, gate)) continue;   // uniform over the block
+        const unsigned tno = item - item0[k], i = tno * BLA + threadIdx.x;
+        double nrm = 0.0;
+        if (i < S.vh) {
+            const R a = R(S.s->alpha);
+            const RY ay = RY(S.s->alpha);
+            Spinor<R> pv, av, rv;
+            Spinor<RY> yv;
+            SpinorIO<P>::load(S.f[R_P], S.vh, i, pv);
+            SpinorIO<P>::load(S.f[R_AP], S.vh, i, av);
+            SpinorIO<P>::load(S.f[R_R], S.vh, i, rv);
+            SpinorIO<PY>::load(S.f[R_Y], S.vh, i, yv);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    yv[sp][c].re += ay * RY(pv[sp][c].re);
+                    yv[sp][c].im += ay * RY(pv[sp][c].im);
+                    rv[sp][c].re -= a * av[sp][c].re;
+                    rv[sp][c].im -= a * av[sp][c].im;
+                }
+            SpinorIO<PY>::store(S.f[R_Y], S.vh, i, yv);
+            SpinorIO<P>::store(S.f[R_R], S.vh, i, rv);
+            nrm = norm2(rv);
+        }
+        double sum = block_sum(nrm, red);
+        if (threadIdx.x == 0) S.partials[tno] = sum;
+    }
+}
+
+// p = r + beta p (restart: p = r)
+template <int P>
+__global__ void __launch_bounds__(BLA) k_batch_pupdate(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+                                                       unsigned nitems, int gate, int restart)
+{
+    using R = typename SpinorIO<P>::R;
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int k = find_sys(item0, nsys, item);
+        const BSys &S = sys[k];
+        if (gated(S.s, gate)) continue;
+        const unsigned i = (item - item0[k]) * BLA + threadIdx.x;
+        if (i >= S.vh) continue;
+        Spinor<R> rv, pv;
+        SpinorIO<P>::load(S.f[R_R], S.vh, i, rv);
+        if (!restart) {
+            const R b = R(S.s->rr_new / S.s->rr);
+            SpinorIO<P>::load(S.f[R_P], S.vh, i, pv);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    rv[sp][c].re += b * pv[sp][c].re;
+                    rv[sp][c].im += b * pv[sp][c].im;
+                }
+        }
+        SpinorIO<P>::store(S.f[R_P], S.vh, i, rv);
+    }
+}
+
+// x += y (FP64), y = 0
+template <int PY>
+__global__ void __launch_bounds__(BLA) k_batch_accum(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+                                                     unsigned nitems, int gate)
+{
+    using RY = typename SpinorIO<PY>::R;
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int k = find_sys(item0, nsys, item);
+        const BSys &S = sys[k];
+        if (gated(S.s, gate)) continue;
+        const unsigned i = (item - item0[k]) * BLA + threadIdx.x;
+        if (i >= S.vh) continue;
+        Spinor<double> xv;
+        Spinor<RY> yv, z;
+        SpinorIO<F64>::load(S.f[R_X], S.vh, i, xv);
+        SpinorIO<PY>::load(S.f[R_Y], S.vh, i, yv);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xv[sp][c].re += double(yv[sp][c].re);
+                xv[sp][c].im += double(yv[sp][c].im);
+                z[sp][c] = {RY(0), RY(0)};
+            }
+        SpinorIO<F64>::store(S.f[R_X], S.vh, i, xv);
+        SpinorIO<PY>::store(S.f[R_Y], S.vh, i, z);
+    }
+}
+
+// r_lo = b - Ax in precision P (FP64 arithmetic), partial |b - Ax|^2
+template <int P>
+__global__ void __launch_bounds__(BLA) k_batch_residual(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+                                                        unsigned nitems, int gate)
+{
+    using R = typename SpinorIO<P>::R;
+    __shared__ double red[BLA];
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int k = find_sys(item0, nsys, item);
+        const BSys &S = sys[k];
+        if (gated(S.s, gate)) continue;
+        const unsigned tno = item - item0[k], i = tno * BLA + threadIdx.x;
+        double nrm = 0.0;
+        if (i < S.vh) {
+            Spinor<double> bv, av;
+            SpinorIO<F64>::load(S.f[R_B], S.vh, i, bv);
+            SpinorIO<F64>::load(S.f[R_AX], S.vh, i, av);
+            Spinor<R> lo;
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    bv[sp][c].re -= av[sp][c].re;
+                    bv[sp][c].im -= av[sp][c].im;
+                    lo[sp][c] = {R(bv[sp][c].re), R(bv[sp][c].im)};
+                }
+            SpinorIO<P>::store(S.f[R_R], S.vh, i, lo);
+            nrm = norm2(bv);
+        }
+        double sum = block_sum(nrm, red);
+        if (threadIdx.x == 0) S.partials[tno] = sum;
+    }
+}
+
+// partial |f|^2 of an FP64 field
+__global__ void __launch_bounds__(BLA) k_batch_norm(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+                                                    unsigned nitems, int role)
+{
+    __shared__ double red[BLA];
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int k = find_sys(item0, nsys, item);
+        const BSys &S = sys[k];
+        const unsigned tno = item - item0[k], i = tno * BLA + threadIdx.x;
+        double nrm = 0.0;
+        if (i < S.vh) {
+            Spinor<double> v;
+            SpinorIO<F64>::load(S.f[role], S.vh, i, v);
+            nrm = norm2(v);
+        }
+        double sum = block_sum(nrm, red);
+        if (threadIdx.x == 0) S.partials[tno] = sum;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(BLA) k_batch_zero(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+                                                    unsigned nitems, int role)
+{
+    using R = typename SpinorIO<P>::R;
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int k = find_sys(item0, nsys, item);
+        const BSys &S = sys[k];
+        const unsigned i = (item - item0[k]) * BLA + threadIdx.x;
+        if (i >= S.vh) continue;
+        Spinor<R> z;
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) z[sp][c] = {R(0), R(0)};
+        SpinorIO<P>::store(S.f[role], S.vh, i, z);
+    }
+}
+
+// One CTA per system: sums its partials (tiles of tile_sites sites) in index
+// order and finishes `op`.
+__global__ void __launch_bounds__(BLA) k_batch_finish(const BSys *__restrict__ sys, int nsys, unsigned tile_sites, int op,
+                                                      int gate)
+{
+    __shared__ double red[BLA];
+    const BSys &S = sys[blockIdx.x];
+    if (gated(S.s, gate)) return;
+    const unsigned n = (S.vh + tile_sites - 1) / tile_sites;
+    double acc = 0.0;
+    for (unsigned t = threadIdx.x; t < n; t += BLA) acc += S.partials[t];
+    double sum = block_sum(acc, red);
+    if (threadIdx.x == 0) cg_finish(op, sum, S.s);
+}
+
+// ------------------------------------------------------------------ host side
+namespace {
+
+struct HopTable {
+    int nrb = 1;            // right-hand sides per pass (1: no link staging)
+    unsigned grid = 0;      // persistent CTAs
+    unsigned nitems = 0;
+    BGroup *dev = nullptr;  // device copy of the groups
+    int ngroups = 0;
+};
+
+struct Batch {
+    int nsys = 0, ngroups = 0;
+    int P = F64, recon_lo = 18, recon_hi = 18, PY = F64;
+    std::vector<BGroup> groups_lo, groups_hi;   // host templates (links set per precision)
+    std::vector<int> order;                     // batch position -> caller's system index
+    BSys *sys = nullptr;                        // device array
+    unsigned *la_item0 = nullptr;               // device prefix table of vector-kernel items
+    unsigned la_items = 0, la_grid = 0;
+    HopTable lo, hi;
+};
+
+unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
+
+template <int P, int RECON, int NRB>
+cudaError_t hop_nrb(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
+                    int gate, cudaStream_t st)
+{
+    if (norm)
+        k_batch_hop<P, RECON, NRB, true><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+    else
+        k_batch_hop<P, RECON, NRB, false><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+    return cudaGetLastError();
+}
+
+template <int P, int RECON>
+cudaError_t hop_pr(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
+                   int gate, cudaStream_t st)
+{
+    switch (t.nrb) {
+    case 1: return hop_nrb<P, RECON, 1>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case 2:
+        // FP64 tiles of 64 sites would exceed 48 KB of static shared memory
+        if constexpr (P != F64) return hop_nrb<P, RECON, 2>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+        return cudaErrorInvalidValue;
+    case 4: return hop_nrb<P, RECON, 4>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case 8: return hop_nrb<P, RECON, 8>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t bhop(int prec, int recon, const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx,
+                 const Coef &k, bool norm, int gate, cudaStream_t st)
+{
+    if (t.nitems == 0) return cudaSuccess;
+    switch (prec * 100 + recon) {
+    case F64 * 100 + 18: return hop_pr<F64, 18>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F64 * 100 + 12: return hop_pr<F64, 12>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F32 * 100 + 18: return hop_pr<F32, 18>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F32 * 100 + 12: return hop_pr<F32, 12>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F16 * 100 + 12: return hop_pr<F16, 12>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Valid right-hand-side pass widths for a storage format (static shared memory <= 48 KB).
+std::vector<int> nrb_candidates(int prec, int recon, int nrhs_max)
+{
+    std::vector<int> c{1};
+    if (nrhs_max <= 1) return c;
+    if (prec != F64) c.push_back(2);
+    c.push_back(4);
+    c.push_back(8);
+    (void)recon;
+    return c;
+}
+
+// Fills a hop table for pass width nrb and uploads it to `dev` (capacity ngroups).
+cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_cap, HopTable &t, BGroup *dev,
+                        cudaStream_t st, std::vector<BGroup> &host)
+{
+    host = tmpl;
+    const unsigned ts = BT / nrb;
+    unsigned item = 0;
+    for (auto &g : host) {
+        g.item0 = item;
+        g.ntiles = cdiv(g.g.vh, ts);
+        item += nrb == 1 ? g.ntiles * unsigned(g.nrhs) : g.ntiles;
+    }
+    t.nrb = nrb;
+    t.nitems = item;
+    t.grid = std::max(1u, std::min(item, grid_cap));
+    t.ngroups = int(host.size());
+    t.dev = dev;
+    return cudaMemcpyAsync(dev, host.data(), sizeof(BGroup) * host.size(), cudaMemcpyHostToDevice, st);
+}
+
+// Times a candidate hop table with a (parity 1, rin -> rout) launch; returns ms.
+// rin and rout must be fields of the table's precision.
+float time_table(int prec, int recon, const HopTable &t, const BSys *sys, int rin, int rout, cudaStream_t st)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    Coef k = coef_plain();
+    bhop(prec, recon, t, sys, 1, rin, rout, -1, k, false, 0, st);
+    cudaEventRecord(a, st);
+    for (int r = 0; r < 3; ++r) bhop(prec, recon, t, sys, 1, rin, rout, -1, k, false, 0, st);
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+}
+
+}  // namespace
+
+// Picks the pass width and persistent grid of a batched hop by timing, with a
+// per-context cache keyed by precision and the shape of the batch.
+cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<BGroup> &tmpl, BGroup *dev,
+                           const BSys *sys, int rin, int rout, HopTable &out, cudaStream_t st)
+{
+    int nrhs_max = 0;
+    std::string key = "bhop/" + std::to_string(prec) + "/" + std::to_string(recon);
+    for (auto &g : tmpl) {
+        nrhs_max = std::max(nrhs_max, g.nrhs);
+        key += "/" + std::to_string(g.g.vh) + "x" + std::to_string(g.nrhs);
+    }
+    const unsigned sms = unsigned(std::max(1, ctx->sm_count));
+    std::vector<BGroup> host;
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        cudaError_t e = build_table(tmpl, it->second.first, it->second.second, out, dev, st, host);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return e;
+    }
+    float best = 1e30f;
+    int best_nrb = 1;
+    unsigned best_cap = 1u << 30;
+    const unsigned caps[] = {sms * 4, sms * 8, sms * 16, 1u << 30};
+    for (int nrb : nrb_candidates(prec, recon, nrhs_max)) {
+        for (unsigned cap : caps) {
+            HopTable t;
+            cudaError_t e = build_table(tmpl, nrb, cap, t, dev, st, host);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            float ms = ctx->autotune ? time_table(prec, recon, t, sys, rin, rout, st) : 0.f;
+            if (ms < best) {
+                best = ms;
+                best_nrb = nrb;
+                best_cap = cap;
+            }
+            if (!ctx->autotune) break;
+        }
+        if (!ctx->autotune) {
+            best_nrb = nrhs_max > 1 ? 4 : 1;
+            break;
+        }
+    }
+    ctx->tuned[key] = {best_nrb, best_cap};
+    cudaError_t e = build_table(tmpl, best_nrb, best_cap, out, dev, st, host);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+}  // namespace twm
+
+using namespace twm;
+
+namespace {
+
+tm_status bfail(tm_ctx *ctx, tm_status st, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+tm_status bcuda(tm_ctx *ctx, cudaError_t e, const char *where)
+{
+    if (ctx) ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return TM_ERR_CUDA;
+}
+
+size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Groups the systems by gauge handle (first appearance order) and fills the
+// group templates; order[k] is the caller's index of batch position k.
+tm_status group_systems(tm_ctx *ctx, int nsys, const tm_gauge *const *U, std::vector<const tm_gauge *> &handles,
+                        std::vector<std::vector<int>> &members)
+{
+    for (int k = 0; k < nsys; ++k) {
+        if (!U[k]) return bfail(ctx, TM_ERR_ARG, "batch: null gauge handle");
+        size_t g = 0;
+        while (g < handles.size() && handles[g] != U[k]) ++g;
+        if (g == handles.size()) {
+            handles.push_back(U[k]);
+            members.emplace_back();
+        }
+        members[g].push_back(k);
+    }
+    return TM_OK;
+}
+
+}  // namespace
+
+extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U, void *const *out_e,
+                                  const void *const *in_e, double kappa, double mu, int sign, void *stream)
+{
+    if (!ctx) return TM_ERR_ARG;
+    if (nsys < 1 || !U || !out_e || !in_e) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad arguments");
+    if (sign != 1 && sign != -1) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: sign must be +1 or -1");
+    std::vector<const tm_gauge *> handles;
+    std::vector<std::vector<int>> members;
+    tm_status st = group_systems(ctx, nsys, U, handles, members);
+    if (st != TM_OK) return st;
+    const int prec = handles[0]->prec, recon = handles[0]->recon;
+    for (auto *h : handles)
+        if (h->prec != prec || h->recon != recon)
+            return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_Qtm_batch: all gauge handles need the same precision and reconstruction");
+    for (int k = 0; k < nsys; ++k) {
+        if (!out_e[k] || !in_e[k] || out_e[k] == in_e[k]) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad field pointer");
+    }
+    // workspace: odd temporaries, system table, group table
+    size_t need = 0;
+    for (int k = 0; k < nsys; ++k) need += al256(spinor_bytes(U[k]->geom.vh, prec));
+    need += al256(sizeof(BSys) * nsys) + al256(sizeof(BGroup) * handles.size());
+    void *base = nullptr;
+    st = tm_ctx_scratch(ctx, need, &base);
+    if (st != TM_OK) return st;
+    char *c = static_cast<char *>(base);
+    std::vector<BSys> hs;
+    std::vector<BGroup> tmpl;
+    std::vector<void *> tmp(nsys);
+    for (int k = 0; k < nsys; ++k) {
+        tmp[k] = c;
+        c += al256(spinor_bytes(U[k]->geom.vh, prec));
+    }
+    for (size_t g = 0; g < handles.size(); ++g) {
+        BGroup G{};
+        G.g = handles[g]->geom;
+        G.links = handles[g]->links;
+        G.nrhs = int(members[g].size());
+        G.sys0 = int(hs.size());
+        tmpl.push_back(G);
+        for (int k : members[g]) {
+            BSys S{};
+            S.f[R_IN] = const_cast<void *>(in_e[k]);
+            S.f[R_OUT] = out_e[k];
+            S.f[R_T] = tmp[k];
+            S.vh = U[k]->geom.vh;
+            hs.push_back(S);
+        }
+    }
+    BSys *dsys = reinterpret_cast<BSys *>(c);
+    c += al256(sizeof(BSys) * nsys);
+    BGroup *dgrp = reinterpret_cast<BGroup *>(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(dsys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
+    HopTable t;
+    if (e == cudaSuccess) e = tune_hop_table(ctx, prec, recon, tmpl, dgrp, dsys, R_IN, R_T, t, s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: setup");
+    const double mut = 2.0 * kappa * mu * sign;
+    tm_trace_mark(ctx, 0, s);
+    e = bhop(prec, recon, t, dsys, 1, R_IN, R_T, -1, coef_qtm_a(mut), false, 0, s);
+    tm_trace_mark(ctx, 1, s);
+    if (e == cudaSuccess) e = bhop(prec, recon, t, dsys, 0, R_T, R_OUT, R_IN, coef_qtm_b(kappa, mut), false, 0, s);
+    tm_trace_mark(ctx, 2, s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: launch");
+    // the tables live in scratch: keep them until the launches have read them
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch");
+    return TM_OK;
+}
+
+extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U_hi, const tm_gauge *const *U_lo,
+                                       void *const *x_dev, const void *const *b_dev, const tm_cg_params *prm,
+                                       tm_cg_info *info, void *stream)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    if (!ctx) return TM_ERR_ARG;
+    if (nsys < 1 || !U_hi || !x_dev || !b_dev || !prm) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad arguments");
+    if (!(prm->tol > 0.0) || prm->maxiter < 0 || prm->reliable_every < 1 || !(prm->reliable_delta >= 0.0) ||
+        !(prm->reliable_delta < 1.0))
+        return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad solver parameters");
+    std::vector<const tm_gauge *> handles;
+    std::vector<std::vector<int>> members;
+    tm_status st = group_systems(ctx, nsys, U_hi, handles, members);
+    if (st != TM_OK) return st;
+    // inner handles: one per group, same precision everywhere
+    std::vector<const tm_gauge *> lo(handles.size());
+    for (size_t g = 0; g < handles.size(); ++g) {
+        if (handles[g]->prec != TM_F64) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi must be FP64 handles");
+        for (int k : members[g]) {
+            const tm_gauge *l = (U_lo && U_lo[k]) ? U_lo[k] : U_hi[k];
+            if (lo[g] && lo[g] != l) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: systems sharing U_hi need the same U_lo");
+            lo[g] = l;
+            if (memcmp(l->dims, handles[g]->dims, sizeof l->dims) || memcmp(l->bc, handles[g]->bc, sizeof l->bc))
+                return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi and U_lo describe different lattices");
+            if (!x_dev[k] || !b_dev[k] || x_dev[k] == b_dev[k]) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad field pointer");
+        }
+    }
+    for (size_t g = 0; g < handles.size(); ++g)
+        if (lo[g]->prec != lo[0]->prec || lo[g]->recon != lo[0]->recon || handles[g]->recon != handles[0]->recon)
+            return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_cg_QdagQ_batch: all systems need the same storage formats");
+
+    Batch B;
+    B.nsys = nsys;
+    B.ngroups = int(handles.size());
+    B.P = lo[0]->prec;
+    B.recon_lo = lo[0]->recon;
+    B.recon_hi = handles[0]->recon;
+    B.PY = B.P == F16 ? F32 : B.P;
+
+    // workspace per system: inner r, p, Ap, q, t; y; FP64 ax, t_hi, q_hi; partials; scalars
+    std::vector<size_t> sys_bytes(nsys);
+    size_t need = 0;
+    for (int k = 0; k < nsys; ++k) {
+        unsigned vh = U_hi[k]->geom.vh;
+        size_t fl = al256(spinor_bytes(vh, B.P)), fy = al256(spinor_bytes(vh, B.PY)), f64 = al256(spinor_bytes(vh, F64));
+        sys_bytes[k] = 5 * fl + fy + 3 * f64 + al256(sizeof(double) * (vh / 16 + 2)) + al256(sizeof(CgScalars));
+        need += sys_bytes[k];
+    }
+    need += al256(sizeof(BSys) * nsys) + 2 * al256(sizeof(BGroup) * handles.size()) + al256(sizeof(unsigned) * (nsys + 1));
+    void *base = nullptr;
+    st = tm_ctx_workspace(ctx, need, &base);
+    if (st != TM_OK) return st;
+    char *c = static_cast<char *>(base);
+    auto take = [&](size_t n) { void *p = c; c += al256(n); return p; };
+
+    std::vector<BSys> hs;
+    std::vector<BGroup> tl, th;
+    std::vector<unsigned> item0;
+    unsigned la_items = 0;
+    for (size_t g = 0; g < handles.size(); ++g) {
+        BGroup G{};
+        G.g = handles[g]->geom;
+        G.nrhs = int(members[g].size());
+        G.sys0 = int(hs.size());
+        G.links = lo[g]->links;
+        tl.push_back(G);
+        G.links = handles[g]->links;
+        th.push_back(G);
+        for (int k : members[g]) {
+            unsigned vh = G.g.vh;
+            BSys S{};
+            S.vh = vh;
+            S.f[R_X] = x_dev[k];
+            S.f[R_B] = const_cast<void *>(b_dev[k]);
+            S.f[R_R] = take(spinor_bytes(vh, B.P));
+            S.f[R_P] = take(spinor_bytes(vh, B.P));
+            S.f[R_AP] = take(spinor_bytes(vh, B.P));
+            S.f[R_Q] = take(spinor_bytes(vh, B.P));
+            S.f[R_T] = take(spinor_bytes(vh, B.P));
+            S.f[R_Y] = take(spinor_bytes(vh, B.PY));
+            S.f[R_AX] = take(spinor_bytes(vh, F64));
+            S.f[R_THI] = take(spinor_bytes(vh, F64));
+            S.f[R_QHI] = take(spinor_bytes(vh, F64));
+            S.partials = static_cast<double *>(take(sizeof(double) * (vh / 16 + 2)));
+            S.s = static_cast<CgScalars *>(take(sizeof(CgScalars)));
+            hs.push_back(S);
+            B.order.push_back(k);
+            item0.push_back(la_items);
+            la_items += cdiv(vh, BLA);
+        }
+    }
+    item0.push_back(la_items);
+    B.sys = static_cast<BSys *>(take(sizeof(BSys) * nsys));
+    BGroup *dlo = static_cast<BGroup *>(take(sizeof(BGroup) * handles.size()));
+    BGroup *dhi = static_cast<BGroup *>(take(sizeof(BGroup) * handles.size()));
+    B.la_item0 = static_cast<unsigned *>(take(sizeof(unsigned) * (nsys + 1)));
+    B.la_items = la_items;
+    B.la_grid = std::min(la_items, unsigned(std::max(1, ctx->sm_count)) * 8u);
+
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<CgScalars> hsc(nsys);
+    for (auto &h : hsc) {
+        h = CgScalars{};
+        h.tol2 = prm->tol * prm->tol;
+        h.maxiter = prm->maxiter;
+        h.delta2 = prm->reliable_delta * prm->reliable_delta;
+        h.every = prm->reliable_every;
+        h.mixed = 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(B.sys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
+    for (int k = 0; k < nsys && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(hs[k].s, &hsc[k], sizeof(CgScalars), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B.la_item0, item0.data(), sizeof(unsigned) * (nsys + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // tuning launches read whatever the work fields hold and write scratch fields of the same precision
+    if (e == cudaSuccess) e = tune_hop_table(ctx, B.P, B.recon_lo, tl, dlo, B.sys, R_P, R_T, B.lo, s);
+    if (e == cudaSuccess) e = tune_hop_table(ctx, F64, B.recon_hi, th, dhi, B.sys, R_AX, R_THI, B.hi, s);
+    if (e != cudaSuccess) return bcuda(ctx, e, "tm_cg_QdagQ_batch: setup");
+
+    const double kappa = prm->kappa, mut = 2.0 * prm->kappa * prm->mu;
+    const unsigned G = B.la_grid, NI = B.la_items;
+    BSys *SY = B.sys;
+    unsigned *I0 = B.la_item0;
+    auto finish = [&](unsigned tile_sites, int op, int gate, cudaStream_t q) {
+        k_batch_finish<<<nsys, BLA, 0, q>>>(SY, nsys, tile_sites, op, gate);
+        return cudaGetLastError();
+    };
+    auto hop_tile = [&](const HopTable &t) { return unsigned(BT / t.nrb); };
+    // ax = Q^dag Q x in FP64 for the systems the gate lets through
+    auto qdagq_hi = [&](int gate, cudaStream_t q) {
+        cudaError_t r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_X, R_THI, -1, coef_qtm_a(mut), false, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_QHI, R_X, coef_qtm_b(kappa, mut), false, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_QHI, R_THI, -1, coef_qtm_a(-mut), false, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_AX, R_QHI, coef_qtm_b(kappa, -mut), false, gate, q);
+        return r;
+    };
+    auto residual = [&](int gate, cudaStream_t q) {
+        if (B.P == F64) k_batch_residual<F64><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, gate);
+        else if (B.P == F32) k_batch_residual<F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, gate);
+        else k_batch_residual<F16><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, gate);
+        cudaError_t r = cudaGetLastError();
+        if (r == cudaSuccess) r = finish(BLA, FIN_RR_TRUE, gate, q);
+        return r;
+    };
+    auto pupdate = [&](int gate, int restart, cudaStream_t q) {
+        if (B.P == F64) k_batch_pupdate<F64><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, gate, restart);
+        else if (B.P == F32) k_batch_pupdate<F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, gate, restart);
+        else k_batch_pupdate<F16><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, gate, restart);
+        cudaError_t r = cudaGetLastError();
+        if (r == cudaSuccess) r = finish(BLA, FIN_ROLL, gate, q);
+        return r;
+    };
+    auto iteration = [&](cudaStream_t q) {
+        cudaError_t r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_P, R_T, -1, coef_qtm_a(mut), false, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_Q, R_P, coef_qtm_b(kappa, mut), true, 1, q);
+        if (r == cudaSuccess) r = finish(hop_tile(B.lo), FIN_PAP, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_Q, R_T, -1, coef_qtm_a(-mut), false, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_AP, R_Q, coef_qtm_b(kappa, -mut), false, 1, q);
+        if (r != cudaSuccess) return r;
+        if (B.P == F64) k_batch_update<F64, F64><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);
+        else if (B.P == F32) k_batch_update<F32, F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);
+        else k_batch_update<F16, F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);
+        r = cudaGetLastError();
+        if (r == cudaSuccess) r = finish(BLA, FIN_RR_UPDATE, 1, q);
+        // reliable update where due: x += y, r = b - Q^dag Q x in FP64
+        if (r == cudaSuccess) {
+            if (B.PY == F64) k_batch_accum<F64><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 2);
+            else k_batch_accum<F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 2);
+            r = cudaGetLastError();
+        }
+        if (r == cudaSuccess) r = qdagq_hi(2, q);
+        if (r == cudaSuccess) r = residual(2, q);
+        if (r == cudaSuccess) r = pupdate(1, 0, q);
+        return r;
+    };
+
+    // setup: |b|^2, r = b - Q^dag Q x, p = r, y = 0
+    k_batch_norm<<<G, BLA, 0, s>>>(SY, I0, nsys, NI, R_B);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = finish(BLA, FIN_BB, 0, s);
+    if (e == cudaSuccess) e = qdagq_hi(0, s);
+    if (e == cudaSuccess) e = residual(0, s);
+    if (e == cudaSuccess) e = pupdate(0, 1, s);
+    if (e == cudaSuccess) {
+        if (B.PY == F64) k_batch_zero<F64><<<G, BLA, 0, s>>>(SY, I0, nsys, NI, R_Y);
+        else k_batch_zero<F32><<<G, BLA, 0, s>>>(SY, I0, nsys, NI, R_Y);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return bcuda(ctx, e, "tm_cg_QdagQ_batch: setup launches");
+
+    const int K = prm->reliable_every;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    if (prm->use_graph) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaSuccess;
+            for (int j = 0; j < K && e1 == cudaSuccess; ++j) e1 = iteration(cap);
+            e = cudaStreamEndCapture(cap, &graph);
+            if (e == cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (cap) cudaStreamDestroy(cap);
+            return bcuda(ctx, e, "tm_cg_QdagQ_batch: graph capture");
+        }
+    }
+
+    int stalled = 0;
+    for (;;) {
+        for (int k = 0; k < nsys && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(&hsc[k], hs[k].s, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        bool all_done = true;
+        for (auto &h : hsc) all_done = all_done && (h.done || h.status != TM_OK);
+        if (all_done) break;
+        int before = 0;
+        for (auto &h : hsc) before += h.iters;
+        e = exec ? cudaGraphLaunch(exec, s) : cudaSuccess;
+        for (int j = 0; !exec && j < K && e == cudaSuccess; ++j) e = iteration(s);
+        if (e != cudaSuccess) break;
+        for (int k = 0; k < nsys && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(&hsc[k], hs[k].s, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        int after = 0;
+        for (auto &h : hsc) after += h.iters;
+        stalled = after == before ? stalled + 1 : 0;
+        if (stalled >= 2) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return bcuda(ctx, e, "tm_cg_QdagQ_batch: iteration");
+
+    tm_status result = TM_OK;
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    for (int pos = 0; pos < nsys; ++pos) {
+        const CgScalars &h = hsc[pos];
+        tm_cg_info inf{};
+        const double target = h.tol2 * h.bb;
+        tm_status r = TM_OK;
+        if (h.status != TM_OK || !std::isfinite(h.rr_true)) r = TM_ERR_NONFINITE;
+        else if (h.rr_true > target) r = TM_ERR_NOT_CONVERGED;
+        inf.iters = h.iters;
+        inf.reliable_updates = h.nreliable;
+        inf.true_relres = h.bb > 0 ? std::sqrt(h.rr_true / h.bb) : 0.0;
+        inf.seconds = secs;
+        inf.status = r;
+        if (info) info[B.order[pos]] = inf;
+        if (r == TM_ERR_NONFINITE) result = r;
+        else if (r == TM_ERR_NOT_CONVERGED && result == TM_OK) result = r;
+    }
+    if (result != TM_OK) ctx->err = result == TM_ERR_NONFINITE ? "tm_cg_QdagQ_batch: non-finite residual"
+                                                               : "tm_cg_QdagQ_batch: maxiter reached";
+    return result;
+}

@@ -130,6 +130,13 @@ template <typename T> inline T ld_keep(const T *p) { return *p; }
 template <typename T> inline T ld_stream(const T *p) { return *p; }
 template <typename T> inline void st_stream(T *p, T v) { *p = v; }
 #endif
+// Link loads: streaming (evict-first) from global memory, or plain (e.g. from
+// a tile staged in shared memory).
+template <bool STREAM, typename T> TM_HD T ld_link(const T *p)
+{
+    if (STREAM) return ld_stream(p);
+    return *p;
+}
 
 // Spinor storage of one parity (component-major, Vh sites per array).
 template <int P> struct SpinorIO;
@@ -245,11 +252,11 @@ template <> struct LinkIO<F64, 18> {
     using R = double;
     using V = double2;
     static constexpr int NCHUNK = 9;
-    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    template <bool STREAM = true> TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
     {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            V v = ld_stream(blk + size_t(k) * vh + i);
+            V v = ld_link<STREAM>(blk + size_t(k) * vh + i);
             u[k / 3][k % 3] = {v.x, v.y};
         }
     }
@@ -263,11 +270,11 @@ template <> struct LinkIO<F64, 12> {
     using R = double;
     using V = double2;
     static constexpr int NCHUNK = 6;
-    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    template <bool STREAM = true> TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
     {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            V v = ld_stream(blk + size_t(k) * vh + i);
+            V v = ld_link<STREAM>(blk + size_t(k) * vh + i);
             u[k / 3][k % 3] = {v.x, v.y};
         }
         reconstruct_row2(u);
@@ -282,11 +289,11 @@ template <> struct LinkIO<F32, 18> {
     using R = float;
     using V = float2;
     static constexpr int NCHUNK = 9;
-    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    template <bool STREAM = true> TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
     {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            V v = ld_stream(blk + size_t(k) * vh + i);
+            V v = ld_link<STREAM>(blk + size_t(k) * vh + i);
             u[k / 3][k % 3] = {v.x, v.y};
         }
     }
@@ -300,11 +307,11 @@ template <> struct LinkIO<F32, 12> {
     using R = float;
     using V = float4;
     static constexpr int NCHUNK = 3;
-    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    template <bool STREAM = true> TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
     {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            V v = ld_stream(blk + size_t(k) * vh + i);
+            V v = ld_link<STREAM>(blk + size_t(k) * vh + i);
             u[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
             u[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
         }
@@ -322,11 +329,11 @@ template <> struct LinkIO<F16, 12> {
     using R = float;
     using V = uint2;
     static constexpr int NCHUNK = 3;
-    TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    template <bool STREAM = true> TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
     {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            V v = ld_stream(blk + size_t(k) * vh + i);
+            V v = ld_link<STREAM>(blk + size_t(k) * vh + i);
             float2 a = __half22float2(*reinterpret_cast<__half2 *>(&v.x));
             float2 b = __half22float2(*reinterpret_cast<__half2 *>(&v.y));
             u[(2 * k) / 3][(2 * k) % 3] = {a.x, a.y};
@@ -411,26 +418,57 @@ template <typename R> TM_HD void negate_half(Half<R> &h)
         for (int c = 0; c < 3; ++c) h[s][c] = -h[s][c];
 }
 
-// One direction mu of the hop at output site i (parity p), added into acc.
-// Forward: (1 - gamma_mu) U_mu(x) psi(x+mu); backward (1 + gamma_mu)
-// U_mu(x-mu)^dag psi(x-mu).  DAG swaps the two projectors, which gives the
-// adjoint hop gamma5 Dhop gamma5 = Dhop^dag.
-template <int P, int RECON, bool DAG, int MU>
-TM_HD void hop_dir(const Geom &g, int p, unsigned i, const Nbrs &n, const typename LinkIO<P, RECON>::V *links,
-                   const void *in, Spinor<typename SpinorIO<P>::R> &acc)
+// Where the hop finds its links.  GlobalLinks reads the forward link
+// U_mu(x) at the output site's index and the backward link U_mu(x-mu) at
+// the neighbour's index from the packed gauge field; StagedLinks reads both
+// from a tile [8 directions][NCHUNK][ts sites] that the block has copied to
+// shared memory (forward mu at 0..3, backward at 4..7).
+template <int P, int RECON> struct GlobalLinks {
+    using L = LinkIO<P, RECON>;
+    const typename L::V *links;
+    unsigned vh, i;
+    int p;
+    template <int MU> TM_HD void fwd(const Nbrs &, Link<typename SpinorIO<P>::R> &u) const
+    {
+        L::load(links + size_t(4 * p + MU) * L::NCHUNK * vh, vh, i, u);
+    }
+    template <int MU> TM_HD void bwd(const Nbrs &n, Link<typename SpinorIO<P>::R> &u) const
+    {
+        L::load(links + size_t(4 * (1 - p) + MU) * L::NCHUNK * vh, vh, n.bwd[MU], u);
+    }
+};
+
+template <int P, int RECON> struct StagedLinks {
+    using L = LinkIO<P, RECON>;
+    const typename L::V *tile;
+    unsigned ts, s;
+    template <int MU> TM_HD void fwd(const Nbrs &, Link<typename SpinorIO<P>::R> &u) const
+    {
+        L::template load<false>(tile + size_t(MU) * L::NCHUNK * ts, ts, s, u);
+    }
+    template <int MU> TM_HD void bwd(const Nbrs &, Link<typename SpinorIO<P>::R> &u) const
+    {
+        L::template load<false>(tile + size_t(4 + MU) * L::NCHUNK * ts, ts, s, u);
+    }
+};
+
+// One direction mu of the hop at output site i, added into acc.  Forward:
+// (1 - gamma_mu) U_mu(x) psi(x+mu); backward (1 + gamma_mu) U_mu(x-mu)^dag
+// psi(x-mu).  DAG swaps the two projectors, which gives the adjoint hop
+// gamma5 Dhop gamma5 = Dhop^dag.
+template <int P, bool DAG, int MU, class Src>
+TM_HD void hop_dir(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<typename SpinorIO<P>::R> &acc)
 {
     using R = typename SpinorIO<P>::R;
-    using L = LinkIO<P, RECON>;
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
     constexpr int SB = -SF;
-    const size_t blk = size_t(L::NCHUNK) * g.vh;
     {
         Spinor<R> s;
         Half<R> h, r;
         Link<R> u;
         SpinorIO<P>::load(in, g.vh, n.fwd[MU], s);
         project<MU, SF>(s, h);
-        L::load(links + (4 * p + MU) * blk, g.vh, i, u);
+        src.template fwd<MU>(n, u);
         link_mul<false>(u, h, r);
         if (n.wf[MU] && g.anti[MU]) negate_half(r);
         accumulate<MU, SF>(r, acc);
@@ -441,28 +479,36 @@ TM_HD void hop_dir(const Geom &g, int p, unsigned i, const Nbrs &n, const typena
         Link<R> u;
         SpinorIO<P>::load(in, g.vh, n.bwd[MU], s);
         project<MU, SB>(s, h);
-        L::load(links + (4 * (1 - p) + MU) * blk, g.vh, n.bwd[MU], u);
+        src.template bwd<MU>(n, u);
         link_mul<true>(u, h, r);
         if (n.wb[MU] && g.anti[MU]) negate_half(r);
         accumulate<MU, SB>(r, acc);
     }
 }
 
-template <int P, int RECON, bool DAG>
-TM_HD void hop_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, RECON>::V *links, const void *in,
-                    Spinor<typename SpinorIO<P>::R> &acc)
+template <int P, bool DAG, class Src>
+TM_HD void hop_site_src(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<typename SpinorIO<P>::R> &acc)
 {
     using R = typename SpinorIO<P>::R;
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[s][c] = {R(0), R(0)};
+    hop_dir<P, DAG, 0>(g, n, src, in, acc);
+    hop_dir<P, DAG, 1>(g, n, src, in, acc);
+    hop_dir<P, DAG, 2>(g, n, src, in, acc);
+    hop_dir<P, DAG, 3>(g, n, src, in, acc);
+}
+
+// The hop at output site i of parity p with links read from the packed gauge field.
+template <int P, int RECON, bool DAG>
+TM_HD void hop_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, RECON>::V *links, const void *in,
+                    Spinor<typename SpinorIO<P>::R> &acc)
+{
     Nbrs n;
     neighbours(g, p, i, n);
-    hop_dir<P, RECON, DAG, 0>(g, p, i, n, links, in, acc);
-    hop_dir<P, RECON, DAG, 1>(g, p, i, n, links, in, acc);
-    hop_dir<P, RECON, DAG, 2>(g, p, i, n, links, in, acc);
-    hop_dir<P, RECON, DAG, 3>(g, p, i, n, links, in, acc);
+    GlobalLinks<P, RECON> src{links, g.vh, i, p};
+    hop_site_src<P, DAG>(g, n, src, in, acc);
 }
 
 // Site-local epilogue: out_u = a_u hop_u + b_u x_u, out_l = a_l hop_l + b_l x_l

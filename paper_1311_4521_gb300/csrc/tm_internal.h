@@ -4,7 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "tm_device.cuh"
@@ -19,6 +21,8 @@ struct tm_ctx {
     std::vector<cudaEvent_t> trace;  // events recorded at kernel boundaries (tm_ctx_trace)
     void *ws = nullptr;              // solver workspace (grow-only)
     size_t ws_bytes = 0;
+    int autotune = 1;                // time launch configurations on first use
+    std::map<std::string, std::pair<int, unsigned>> tuned;  // batched hop: key -> (pass width, CTA cap)
 };
 
 // Records trace event k of ctx on stream s, if tracing is on.

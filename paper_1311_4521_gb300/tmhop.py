@@ -70,6 +70,9 @@ def _load() -> ctypes.CDLL:
         "tm_Qtm": ([P, P, P, P, D, D, I, P], I),
         "tm_Qtm_noalloc": ([P, P, P, P, D, D, I, P], I),
         "tm_cg_QdagQ": ([P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
+        "tm_ctx_set_autotune": ([P, I], I),
+        "tm_Qtm_batch": ([P, I, P, P, P, D, D, I, P], I),
+        "tm_cg_QdagQ_batch": ([P, I, P, P, P, P, ctypes.POINTER(CgParams), P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -180,6 +183,34 @@ def tm_cg_QdagQ(ctx, U_hi, U_lo, x_dev, b_dev, params: CgParams, stream=None):
     return st, info
 
 
+def tm_ctx_set_autotune(ctx, on: bool) -> None:
+    _check(ctx, lib.tm_ctx_set_autotune(ctx, int(bool(on))))
+
+
+def _parr(items):
+    return (ctypes.c_void_p * len(items))(*[(_ptr(t).value or 0) if not isinstance(t, ctypes.c_void_p) else t.value
+                                            for t in items])
+
+
+def tm_Qtm_batch(ctx, gauges, outs, ins, kappa, mu, sign=1, stream=None):
+    """gauges: list of gauge handles (ctypes pointers), outs/ins: lists of device buffers."""
+    n = len(gauges)
+    _check(ctx, lib.tm_Qtm_batch(ctx, n, _parr(gauges), _parr(outs), _parr(ins), float(kappa), float(mu), int(sign),
+                                 _stream(stream)))
+
+
+def tm_cg_QdagQ_batch(ctx, U_hi, U_lo, xs, bs, params: CgParams, stream=None):
+    """Returns (status, [CgInfo per system]); raises only for argument and CUDA errors."""
+    n = len(U_hi)
+    infos = (CgInfo * n)()
+    lo = _parr(U_lo) if U_lo is not None else None
+    st = lib.tm_cg_QdagQ_batch(ctx, n, _parr(U_hi), lo, _parr(xs), _parr(bs), ctypes.byref(params), infos,
+                               _stream(stream))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE):
+        _check(ctx, st)
+    return st, list(infos)
+
+
 def tm_Qtm_noalloc(ctx, U, out_e_dev, in_e_dev, kappa, mu, sign=1, stream=None):
     """tm_Qtm with its temporary in the library's static device array: no device allocation."""
     _check(ctx, lib.tm_Qtm_noalloc(ctx, U, _ptr(out_e_dev), _ptr(in_e_dev), float(kappa), float(mu), int(sign),
@@ -277,6 +308,19 @@ class Context:
     def Qtm(self, U: Gauge, out, inp, kappa, mu, sign=1):
         tm_Qtm(self.handle, U.handle, out, inp, kappa, mu, sign)
         return out
+
+    def Qtm_batch(self, gauges, outs, ins, kappa, mu, sign=1):
+        tm_Qtm_batch(self.handle, [g.handle for g in gauges], outs, ins, kappa, mu, sign)
+        return outs
+
+    def cg_batch(self, U_hi, xs, bs, kappa, mu, tol=1e-10, maxiter=30000, U_lo=None, reliable_every=50,
+                 use_graph=True, reliable_delta=0.1):
+        """Solves Q^dag Q x[k] = b[k] for all k at once.  Returns (status, [info dict per system])."""
+        prm = CgParams(float(kappa), float(mu), float(tol), int(maxiter), int(reliable_every), int(bool(use_graph)),
+                       float(reliable_delta))
+        st, infos = tm_cg_QdagQ_batch(self.handle, [g.handle for g in U_hi],
+                                      [g.handle for g in U_lo] if U_lo is not None else None, xs, bs, prm)
+        return st, [i.as_dict() for i in infos]
 
     def cg(self, U_hi: Gauge, x, b, kappa, mu, tol=1e-10, maxiter=30000, U_lo: Gauge | None = None,
            reliable_every=50, use_graph=True, reliable_delta=0.1):
