@@ -314,6 +314,11 @@ def gpu_arm(args) -> None:
     if not args.no_cg:
         cg = cg_section(args, ctx, tmhop, torch, F, allmax, barrier)
 
+    # ---- batching: 12 right-hand sides on 32^3x64 and 8 uneven lattices, FP32 storage
+    batch = None
+    if not args.no_batch:
+        batch = batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U if DIMS == (32, 32, 32, 64) else None)
+
     # ---- CPU baseline: the FP64 oracle on this host's cores, same lattice
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -345,7 +350,7 @@ def gpu_arm(args) -> None:
                        "l2": f"inputs larger than L2 ({links_gb:.2f} GB links "
                              f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"},
             "gflops": round(gflops, 2), "roofline": roofline, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "cg": cg,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "cg": cg, "batch": batch,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -388,6 +393,116 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier) -> dict:
     for name in ("mixed_f32", "mixed_f16"):
         out[name]["speedup_vs_fp64"] = round(out["fp64"]["seconds"] / out[name]["seconds"], 2)
     for g in [gh] + list(lo.values()):
+        g.close()
+    return out
+
+
+UNEVEN = [(16, 16, 16, 32), (20, 20, 20, 40), (24, 24, 24, 48), (28, 28, 28, 56), (32, 32, 32, 64),
+          (16, 16, 16, 64), (24, 24, 24, 32), (12, 12, 12, 24)]
+
+
+def batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U32=None) -> dict:
+    """Batching workload, FP32 storage (12-real links): (a) Q_tm on 12
+    right-hand sides of one 32^3x64 lattice in one launch per hop, against 12
+    single Q_tm calls; (b) CG to 1e-10 on the 12 right-hand sides and (c) on
+    8 lattices of uneven volume (sum of V = 5,187,072 sites), each batch in
+    one call against the same systems solved one after the other."""
+    big = (32, 32, 32, 64)
+    vh = int(np.prod(big)) // 2
+    if U32 is None:
+        U32 = F.gauge_field(big, F.SEED_PROD_32, "near", 0.3)
+    g32 = ctx.gauge(big, U32, "f32", 12)
+    g64 = ctx.gauge(big, U32, "f64", 18)
+    rhs = [F.gaussian_spinor(vh, F.SEED_BATCH_RHS + j, 0) for j in range(12)]
+    ins = [ctx.pack(r, "f32") for r in rhs]
+    outs = [ctx.empty(vh, "f32") for _ in rhs]
+    stream = torch.cuda.current_stream()
+    out = {"storage": "f32-12", "kappa": KAPPA, "mu": MU}
+
+    def timed(fn, reps):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return allmax(e0.elapsed_time(e1) / reps)
+
+    reps = max(3, min(50, args.steps // 20))
+    ms_batch = timed(lambda: ctx.Qtm_batch([g32] * 12, outs, ins, KAPPA, MU), reps)
+    ms_single = timed(lambda: [ctx.Qtm(g32, o, i, KAPPA, MU) for o, i in zip(outs, ins)], reps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for e in ev:
+        e.record(stream)
+    tmhop.tm_ctx_trace(ctx.handle, ev)
+    ctx.Qtm_batch([g32] * 12, outs, ins, KAPPA, MU)
+    tmhop.tm_ctx_trace(ctx.handle, None)
+    torch.cuda.synchronize()
+    kb_ms = ev[1].elapsed_time(ev[2])
+    # bytes per even site and right-hand side: 2 hops of (spinor in + out + 8 links / 12) + psi_e re-read
+    per = 2 * (96 + 96 + 384 / 12) + 96
+    out["qtm_12rhs"] = {"ms_batched": round(ms_batch, 4), "ms_12_single_calls": round(ms_single, 4),
+                        "speedup": round(ms_single / ms_batch, 2),
+                        "GBps_algorithmic_amortised_links": round(12 * vh * per / (ms_batch * 1e-3) / 1e9, 1),
+                        "kernel_b_ms": round(kb_ms, 4),
+                        "kernel_b_GBps": round(12 * vh * (96 + 96 + 384 / 12 + 96) / (kb_ms * 1e-3) / 1e9, 1)}
+    del ins, outs
+
+    def solve_batch(gh, gl, bs):
+        xs = [ctx.empty(b.numel() // 192, "f64").zero_() for b in bs]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st, infos = ctx.cg_batch(gh, xs, bs, KAPPA, MU, 1e-10, 30000, gl)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, st, infos
+
+    def solve_each(gh, gl, bs):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        its = []
+        for h, l, b in zip(gh, gl, bs):
+            x = ctx.empty(b.numel() // 192, "f64").zero_()
+            st, inf = ctx.cg(h, x, b, KAPPA, MU, 1e-10, 30000, l)
+            its.append(inf["iters"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, its
+
+    bs = [ctx.pack(r, "f64") for r in rhs]
+    solve_batch([g64] * 12, [g32] * 12, bs)   # warm-up (workspace, tuning)
+    tb, st, infos = solve_batch([g64] * 12, [g32] * 12, bs)
+    solve_each([g64] * 12, [g32] * 12, bs)
+    te, its = solve_each([g64] * 12, [g32] * 12, bs)
+    out["cg_12rhs_32x32x32x64"] = {"seconds_batched": round(allmax(tb), 4), "seconds_one_by_one": round(allmax(te), 4),
+                                   "speedup": round(te / tb, 2), "converged": st == tmhop.TM_OK,
+                                   "iters": [i["iters"] for i in infos],
+                                   "max_true_relres": max(i["true_relres"] for i in infos)}
+    del bs
+    g32.close()
+    g64.close()
+    del U32
+    lats = [(d, F.gauge_field(d, F.SEED_BATCH_LATTICE + k, "near", 0.3)) for k, d in enumerate(UNEVEN)]
+    gh = [ctx.gauge(d, U, "f64", 18) for d, U in lats]
+    gl = [ctx.gauge(d, U, "f32", 12) for d, U in lats]
+    bs = [ctx.pack(F.gaussian_spinor(int(np.prod(d)) // 2, F.SEED_BATCH_LATTICE + k, 1), "f64")
+          for k, (d, _) in enumerate(lats)]
+    del lats
+    solve_batch(gh, gl, bs)
+    tb, st, infos = solve_batch(gh, gl, bs)
+    solve_each(gh, gl, bs)
+    te, its = solve_each(gh, gl, bs)
+    out["cg_8_uneven_lattices"] = {"lattices": [list(d) for d in UNEVEN], "sites": int(sum(np.prod(d) for d in UNEVEN)),
+                                   "seconds_batched": round(allmax(tb), 4), "seconds_one_by_one": round(allmax(te), 4),
+                                   "speedup": round(te / tb, 2), "converged": st == tmhop.TM_OK,
+                                   "iters": [i["iters"] for i in infos],
+                                   "max_true_relres": max(i["true_relres"] for i in infos)}
+    for g in gh + gl:
         g.close()
     return out
 
@@ -446,6 +561,7 @@ def main() -> None:
     ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cg-lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=(48, 48, 48, 96))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

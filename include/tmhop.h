@@ -183,6 +183,25 @@ typedef struct {
 tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gauge *U_lo, void *x_dev, const void *b_dev,
                       const tm_cg_params *params, tm_cg_info *info, void *stream);
 
+/* ---- adjoint: force and gradient ---------------------------------------- */
+
+enum { TM_FORCE_SU3 = 0,    /* F in su(3): U -> exp(eps T) U changes S by eps <T, F>, <A,B> = -2 tr(AB) */
+       TM_FORCE_GRAD = 1 }; /* G = dS/dRe U + i dS/dIm U, the gradient w.r.t. the complex link entries */
+
+/* Fermion force of the action S = phi^dag (Q^dag Q)^-1 phi given the
+ * solution X = (Q^dag Q)^-1 phi, the derivative the HMC integration needs
+ * (the paper's Sec. 2.4 "fermionic derivative").  X_e_dev is a packed even
+ * field in U's precision; F_dev receives complex double [4][V][3][3] in the
+ * canonical gauge layout: for TM_FORCE_SU3 the traceless anti-Hermitian
+ * F_mu(x) = -kappa^2 s TA(U M1 - M2 U^dag), for TM_FORCE_GRAD the complex
+ * gradient 2 kappa^2 s (M1^dag + M2), with M1, M2 the spin-summed outer
+ * products of the projected fields at the two ends of the link and s its
+ * boundary sign.  Three hop launches (Y = Q X and the two odd fields) and
+ * one launch with one thread per link, which writes every link exactly once
+ * (no atomics).  Scratch is owned by ctx. */
+tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa, double mu,
+                   int mode, void *stream);
+
 /* ---- batches ------------------------------------------------------------ */
 
 /* Q_tm(sign*mu) applied to nsys even fields (out_e[k] = Q in_e[k] with gauge

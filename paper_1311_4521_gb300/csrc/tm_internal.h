@@ -67,5 +67,7 @@ int link_nchunk(int prec, int recon);
 Coef coef_plain();
 Coef coef_qtm_a(double mut);
 Coef coef_qtm_b(double kappa, double mut);
+// gamma5 (1 + i mut gamma5) / (1 + mut^2): the odd field B of the force
+Coef coef_force_b(double mut);
 
 }  // namespace twm

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libtmhop.so")
 TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE, TM_ERR_TIMEOUT, TM_ERR_UNSUPPORTED = range(7)
 TM_F64, TM_F32, TM_F16 = 0, 1, 2
 TM_EO, TM_OE = 0, 1
+TM_FORCE_SU3, TM_FORCE_GRAD = 0, 1
 PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16}
 
 
@@ -71,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "tm_Qtm_noalloc": ([P, P, P, P, D, D, I, P], I),
         "tm_cg_QdagQ": ([P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
         "tm_ctx_set_autotune": ([P, I], I),
+        "tm_force": ([P, P, P, P, D, D, I, P], I),
         "tm_Qtm_batch": ([P, I, P, P, P, D, D, I, P], I),
         "tm_cg_QdagQ_batch": ([P, I, P, P, P, P, ctypes.POINTER(CgParams), P, P], I),
     }
@@ -181,6 +183,10 @@ def tm_cg_QdagQ(ctx, U_hi, U_lo, x_dev, b_dev, params: CgParams, stream=None):
     if st not in (TM_OK, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE):
         _check(ctx, st)
     return st, info
+
+
+def tm_force(ctx, U, F_dev, X_e_dev, kappa, mu, mode=TM_FORCE_SU3, stream=None):
+    _check(ctx, lib.tm_force(ctx, U, _ptr(F_dev), _ptr(X_e_dev), float(kappa), float(mu), int(mode), _stream(stream)))
 
 
 def tm_ctx_set_autotune(ctx, on: bool) -> None:
@@ -308,6 +314,13 @@ class Context:
     def Qtm(self, U: Gauge, out, inp, kappa, mu, sign=1):
         tm_Qtm(self.handle, U.handle, out, inp, kappa, mu, sign)
         return out
+
+    def force(self, U: Gauge, X_e, kappa, mu, mode=TM_FORCE_SU3) -> torch.Tensor:
+        """Force (or complex gradient) of S = phi^dag (Q^dag Q)^-1 phi given packed X; (4, V, 3, 3) complex128."""
+        V = 2 * U.vh
+        F = torch.empty((4, V, 3, 3, 2), dtype=torch.float64, device=self.device)
+        tm_force(self.handle, U.handle, F, X_e, kappa, mu, mode)
+        return torch.view_as_complex(F)
 
     def Qtm_batch(self, gauges, outs, ins, kappa, mu, sign=1):
         tm_Qtm_batch(self.handle, [g.handle for g in gauges], outs, ins, kappa, mu, sign)
