@@ -218,6 +218,15 @@ def gpu_arm(args) -> None:
     if uuid and not uuid.startswith("GPU-"):
         uuid = "GPU-" + uuid
 
+    if args.only:
+        out = only_section(args, ctx, tmhop, torch, F, U, psi, DIMS, vh, barrier, allmax)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
     # ---- headline: FP64 storage, 18-real links (by default)
     g = ctx.gauge(DIMS, U, prec, recon)
     src = ctx.pack(psi, prec)
@@ -319,6 +328,11 @@ def gpu_arm(args) -> None:
     if not args.no_batch:
         batch = batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U if DIMS == (32, 32, 32, 64) else None)
 
+    # ---- differentiation: S = phi^dag (Q^dag Q)^-1 phi and dS/dphi, dS/dU on 24^3x48
+    grad = None
+    if not args.no_grad:
+        grad = grad_section(args, ctx, tmhop, torch, F)
+
     # ---- CPU baseline: the FP64 oracle on this host's cores, same lattice
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -350,7 +364,7 @@ def gpu_arm(args) -> None:
                        "l2": f"inputs larger than L2 ({links_gb:.2f} GB links "
                              f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"},
             "gflops": round(gflops, 2), "roofline": roofline, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "cg": cg, "batch": batch,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "cg": cg, "batch": batch, "grad": grad,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -394,6 +408,98 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier) -> dict:
         out[name]["speedup_vs_fp64"] = round(out["fp64"]["seconds"] / out[name]["seconds"], 2)
     for g in [gh] + list(lo.values()):
         g.close()
+    return out
+
+
+def only_section(args, ctx, tmhop, torch, F, U, psi, dims, vh, barrier, allmax) -> dict:
+    """One part of the benchmark alone, for profiling captures:
+    batch-qtm  Q_tm on 12 right-hand sides of --lattice, --steps batched calls;
+    cg         the CG section on --cg-lattice;
+    force      the force kernel on --lattice, --steps calls;
+    solve      the even-odd full-lattice solve on --lattice (FP32 inner)."""
+    res = {"only": args.only, "lattice": list(dims)}
+    stream = torch.cuda.current_stream()
+    if args.only == "batch-qtm":
+        g = ctx.gauge(dims, U, args.prec, args.recon)
+        ins = [ctx.pack(F.gaussian_spinor(vh, F.SEED_BATCH_RHS + j, 0), args.prec) for j in range(12)]
+        outs = [ctx.empty(vh, args.prec) for _ in range(12)]
+        for _ in range(args.warmup):
+            ctx.Qtm_batch([g] * 12, outs, ins, KAPPA, MU)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.Qtm_batch([g] * 12, outs, ins, KAPPA, MU)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["ms_per_batched_qtm"] = e0.elapsed_time(e1) / args.steps
+        g.close()
+    elif args.only == "cg":
+        args.cg_lattice = dims
+        res.update(cg_section(args, ctx, tmhop, torch, F, allmax, barrier))
+    elif args.only == "force":
+        g = ctx.gauge(dims, U, args.prec, args.recon)
+        xp = ctx.pack(psi, args.prec)
+        for _ in range(args.warmup):
+            ctx.force(g, xp, KAPPA, MU)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.force(g, xp, KAPPA, MU)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["ms_per_force"] = e0.elapsed_time(e1) / args.steps
+        g.close()
+    elif args.only == "solve":
+        gh, gl = ctx.gauge(dims, U, "f64", 18), ctx.gauge(dims, U, "f32", 12)
+        be, bo = ctx.pack(psi, "f64"), ctx.pack(F.gaussian_spinor(vh, F.SEED_PROD_32, 2), "f64")
+        xe, xo = ctx.empty(vh, "f64").zero_(), ctx.empty(vh, "f64")
+        st, info = ctx.solve_eo(gh, xe, xo, be, bo, KAPPA, MU, 1e-10, 30000, gl)
+        res.update({"status": st, "info": info})
+        gh.close()
+        gl.close()
+    return res
+
+
+def grad_section(args, ctx, tmhop, torch, F) -> dict:
+    """24^3x48, U = exp(0.3 i A): the action S = phi^dag (Q^dag Q)^-1 phi
+    through autograd (forward solve + backward force), and the force
+    kernel alone, FP64 and FP32 storage (for information: correctness is
+    covered by the tests)."""
+    from paper_1311_4521_gb300 import autograd
+    dims = (24, 24, 24, 48)
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, F.SEED_GRAD_24, "near", 0.3)
+    phi = F.gaussian_spinor(vh, F.SEED_GRAD_24, 1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Ut = torch.from_numpy(U).to(dev).requires_grad_(True)
+    pt = torch.from_numpy(phi).to(dev).requires_grad_(True)
+    out = {"lattice": list(dims), "kappa": KAPPA, "mu": MU}
+    stream = torch.cuda.current_stream()
+    for inner, fprec in (("f64", "f64"), ("f32", "f32")):
+        for rep in range(2):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize()
+            e0.record(stream)
+            S = autograd.action(pt, Ut, dims, KAPPA, MU, tol=1e-10, inner=inner, force_prec=fprec)
+            e1.record(stream)
+            gphi, gU = torch.autograd.grad(S, (pt, Ut))
+            e2.record(stream)
+            torch.cuda.synchronize()
+        g = ctx.gauge(dims, U, fprec, 18 if fprec == "f64" else 12)
+        xp = ctx.pack(gphi.detach() / 2, fprec)
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ctx.force(g, xp, KAPPA, MU)
+        fe[0].record(stream)
+        for _ in range(10):
+            ctx.force(g, xp, KAPPA, MU)
+        fe[1].record(stream)
+        torch.cuda.synchronize()
+        g.close()
+        out[f"{inner}_solve_{fprec}_force"] = {
+            "forward_s": round(e0.elapsed_time(e1) / 1e3, 4), "backward_s": round(e1.elapsed_time(e2) / 1e3, 4),
+            "force_ms": round(fe[0].elapsed_time(fe[1]) / 10, 4), "S": float(S.item())}
     return out
 
 
@@ -562,6 +668,9 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--only", choices=["batch-qtm", "cg", "force", "solve"], default=None,
+                    help="run one section alone (for profiling captures)")
     ap.add_argument("--cg-lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=(48, 48, 48, 96))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

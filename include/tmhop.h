@@ -183,6 +183,16 @@ typedef struct {
 tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gauge *U_lo, void *x_dev, const void *b_dev,
                       const tm_cg_params *params, tm_cg_info *info, void *stream);
 
+/* Solves the full-lattice system M x = b, M = 1 - kappa Dhop + i mut gamma5,
+ * by even-odd preconditioning: bhat_e = b_e + kappa H_eo M_oo^-1 b_o, CG on
+ * Q^dag Q x_e = Q^dag gamma5 bhat_e (tm_cg_QdagQ with the same U_hi, U_lo
+ * and params; x_e in: initial guess), then x_o = M_oo^-1 (b_o + kappa H_oe
+ * x_e).  All four fields are packed FP64 (even: x_e, b_e; odd: x_o, b_o),
+ * pairwise distinct.  info and the return value are those of the even-site
+ * solve; its tolerance applies to the Q^dag Q system.  Synchronous. */
+tm_status tm_solve_eo(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gauge *U_lo, void *x_e, void *x_o, const void *b_e,
+                      const void *b_o, const tm_cg_params *params, tm_cg_info *info, void *stream);
+
 /* ---- adjoint: force and gradient ---------------------------------------- */
 
 enum { TM_FORCE_SU3 = 0,    /* F in su(3): U -> exp(eps T) U changes S by eps <T, F>, <A,B> = -2 tr(AB) */

@@ -79,6 +79,10 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
         const unsigned i = tno * TS + tx;
         const V *links = static_cast<const V *>(G.links);
         if (NRB > 1) {
+            // skip the tile (and its link traffic) when no system of the group is active
+            bool any = false;
+            for (int r = 0; r < G.nrhs && !any; ++r) any = !gated(sys[G.sys0 + r].s, gate);
+            if (!any) continue;   // uniform over the block
             __syncthreads();  // readers of the previous tile are done
             if (ty == 0) {
                 unsigned site = tno * TS + tx;
@@ -168,7 +172,7 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 
 // y += alpha p, r -= alpha Ap, partial |r|^2
 template <int P, int PY>
-__global__ void __launch_bounds__(BLA) k_batch_update(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+__global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_update(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
                                                       unsigned nitems, int gate)
 {
     using R = typename SpinorIO<P>::R;
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(BLA) k_batch_update(const BSys *__restrict__ s
 
 // p = r + beta p (restart: p = r)
 template <int P>
-__global__ void __launch_bounds__(BLA) k_batch_pupdate(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+__global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_pupdate(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
                                                        unsigned nitems, int gate, int restart)
 {
     using R = typename SpinorIO<P>::R;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(BLA) k_batch_pupdate(const BSys *__restrict__ 
 
 // x += y (FP64), y = 0
 template <int PY>
-__global__ void __launch_bounds__(BLA) k_batch_accum(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+__global__ void __launch_bounds__(BLA, 4) k_batch_accum(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
                                                      unsigned nitems, int gate)
 {
     using RY = typename SpinorIO<PY>::R;
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(BLA) k_batch_accum(const BSys *__restrict__ sy
 
 // r_lo = b - Ax in precision P (FP64 arithmetic), partial |b - Ax|^2
 template <int P>
-__global__ void __launch_bounds__(BLA) k_batch_residual(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+__global__ void __launch_bounds__(BLA, 3) k_batch_residual(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
                                                         unsigned nitems, int gate)
 {
     using R = typename SpinorIO<P>::R;
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(BLA) k_batch_residual(const BSys *__restrict__
 }
 
 // partial |f|^2 of an FP64 field
-__global__ void __launch_bounds__(BLA) k_batch_norm(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+__global__ void __launch_bounds__(BLA, 4) k_batch_norm(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
                                                     unsigned nitems, int role)
 {
     __shared__ double red[BLA];
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(BLA) k_batch_norm(const BSys *__restrict__ sys
 }
 
 template <int P>
-__global__ void __launch_bounds__(BLA) k_batch_zero(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
+__global__ void __launch_bounds__(BLA, 4) k_batch_zero(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
                                                     unsigned nitems, int role)
 {
     using R = typename SpinorIO<P>::R;
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(BLA) k_batch_zero(const BSys *__restrict__ sys
 
 // One CTA per system: sums its partials (tiles of tile_sites sites) in index
 // order and finishes `op`.
-__global__ void __launch_bounds__(BLA) k_batch_finish(const BSys *__restrict__ sys, int nsys, unsigned tile_sites, int op,
+__global__ void __launch_bounds__(BLA, 4) k_batch_finish(const BSys *__restrict__ sys, int nsys, unsigned tile_sites, int op,
                                                       int gate)
 {
     __shared__ double red[BLA];

@@ -73,7 +73,7 @@ constexpr int LA_BLOCK = 256;
 
 // Hop with the twisted-mass epilogue; NORM also reduces |out|^2 into pAp.
 template <int P, int RECON, bool NORM>
-__global__ void __launch_bounds__(HOP_BLOCK) k_cg_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,
+__global__ void __launch_bounds__(HOP_BLOCK, TM_HOP_MINB(P)) k_cg_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,
                                                       const void *__restrict__ in, void *__restrict__ out,
                                                       const void *__restrict__ x, Coef k, double *partials,
                                                       CgScalars *s, int gate)
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(HOP_BLOCK) k_cg_hop(Geom g, int p, const typen
 
 // y += alpha p, r -= alpha Ap, rr_new = |r|^2 (y in precision PY).
 template <int P, int PY>
-__global__ void __launch_bounds__(LA_BLOCK) k_cg_update(unsigned vh, void *y, void *r, const void *p, const void *Ap,
+__global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_update(unsigned vh, void *y, void *r, const void *p, const void *Ap,
                                                         double *partials, CgScalars *s)
 {
     using R = typename SpinorIO<P>::R;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(LA_BLOCK) k_cg_update(unsigned vh, void *y, vo
 
 // p = r + beta p with beta = rr_new / rr (restart: p = r); then rr = rr_new.
 template <int P>
-__global__ void __launch_bounds__(LA_BLOCK) k_cg_pupdate(unsigned vh, void *p, const void *r, double *partials,
+__global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_pupdate(unsigned vh, void *p, const void *r, double *partials,
                                                          CgScalars *s, int skip, int restart)
 {
     using R = typename SpinorIO<P>::R;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(LA_BLOCK) k_cg_pupdate(unsigned vh, void *p, c
 
 // x += y (FP64), y = 0.
 template <int PY>
-__global__ void __launch_bounds__(LA_BLOCK) k_cg_accum(unsigned vh, void *x, void *y, const CgScalars *s, int gate)
+__global__ void __launch_bounds__(LA_BLOCK, 4) k_cg_accum(unsigned vh, void *x, void *y, const CgScalars *s, int gate)
 {
     using RY = typename SpinorIO<PY>::R;
     if (gated(s, gate)) return;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(LA_BLOCK) k_cg_accum(unsigned vh, void *x, voi
 
 // res = b - Ax (FP64, may alias Ax); r_lo = res in precision P if given; |res|^2 -> op.
 template <int P>
-__global__ void __launch_bounds__(LA_BLOCK) k_cg_residual(unsigned vh, const void *b, const void *Ax, void *res,
+__global__ void __launch_bounds__(LA_BLOCK, 3) k_cg_residual(unsigned vh, const void *b, const void *Ax, void *res,
                                                           void *r_lo, double *partials, CgScalars *s, int op, int gate)
 {
     using R = typename SpinorIO<P>::R;
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(LA_BLOCK) k_cg_residual(unsigned vh, const voi
 }
 
 // |v|^2 of an FP64 field -> op.
-__global__ void __launch_bounds__(LA_BLOCK) k_cg_norm(unsigned vh, const void *v, double *partials, CgScalars *s, int op)
+__global__ void __launch_bounds__(LA_BLOCK, 4) k_cg_norm(unsigned vh, const void *v, double *partials, CgScalars *s, int op)
 {
     unsigned i = blockIdx.x * LA_BLOCK + threadIdx.x;
     double nrm = 0.0;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(LA_BLOCK) k_cg_norm(unsigned vh, const void *v
 }
 
 template <int P>
-__global__ void __launch_bounds__(LA_BLOCK) k_cg_zero(unsigned vh, void *v)
+__global__ void __launch_bounds__(LA_BLOCK, 4) k_cg_zero(unsigned vh, void *v)
 {
     using R = typename SpinorIO<P>::R;
     unsigned i = blockIdx.x * LA_BLOCK + threadIdx.x;

@@ -27,6 +27,18 @@
 
 #define TM_HD __host__ __device__ __forceinline__
 
+// Resident CTAs per SM the hop kernels are compiled for (registers per
+// thread <= 65536 / (128 x this)).  Measured on GB300 at 32^3x64 (sweep of
+// 4, 5, 6, 8): FP32 storage is fastest at 4 (more registers, more loads in
+// flight per thread), FP16 at 5; FP64 hops are bound by the FP64 pipe.
+#ifndef TM_HOP_MINB_F32
+#define TM_HOP_MINB_F32 4
+#endif
+#ifndef TM_HOP_MINB_F16
+#define TM_HOP_MINB_F16 5
+#endif
+#define TM_HOP_MINB(P) ((P) == 0 ? 2 : (P) == 1 ? TM_HOP_MINB_F32 : TM_HOP_MINB_F16)
+
 namespace twm {
 
 enum { F64 = 0, F32 = 1, F16 = 2 };
@@ -143,6 +155,12 @@ template <int P> struct SpinorIO;
 
 template <> struct SpinorIO<F64> {
     using R = double;
+    // load without the site scale; returns the factor the values must be multiplied by
+    TM_HD static R load_raw(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        load(base, vh, i, s);
+        return R(1);
+    }
     TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
     {
         const double2 *b = static_cast<const double2 *>(base);
@@ -162,6 +180,11 @@ template <> struct SpinorIO<F64> {
 
 template <> struct SpinorIO<F32> {
     using R = float;
+    TM_HD static R load_raw(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        load(base, vh, i, s);
+        return R(1);
+    }
     TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
     {
         const float4 *b = static_cast<const float4 *>(base);
@@ -189,11 +212,11 @@ template <> struct SpinorIO<F32> {
 // norm itself as a float after the three component arrays.
 template <> struct SpinorIO<F16> {
     using R = float;
-    TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    // the stored values (in [-1, 1]) and, as return value, the site norm they are scaled by
+    TM_HD static R load_raw(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
     {
         const uint4 *b = static_cast<const uint4 *>(base);
         const float *nrm = reinterpret_cast<const float *>(b + size_t(3) * vh);
-        float n = ld_keep(nrm + i);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             uint4 v = ld_keep(b + size_t(k) * vh + i);
@@ -203,9 +226,16 @@ template <> struct SpinorIO<F16> {
                 __half2 h = *reinterpret_cast<__half2 *>(&w[q]);
                 float2 f = __half22float2(h);
                 int c = 4 * k + q;
-                s[c / 3][c % 3] = {n * f.x, n * f.y};
+                s[c / 3][c % 3] = {f.x, f.y};
             }
         }
+        return ld_keep(nrm + i);
+    }
+    TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        const R n = load_raw(base, vh, i, s);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) s[c / 3][c % 3] = n * s[c / 3][c % 3];
     }
     TM_HD static void store(void *base, unsigned vh, unsigned i, const Spinor<R> &s)
     {
@@ -373,25 +403,30 @@ template <int MU, int S, typename R> TM_HD void project(const Spinor<R> &p, Half
     }
 }
 
-// acc += (h, s A_mu^dag h), the full spinor rebuilt from its upper pair.
-template <int MU, int S, typename R> TM_HD void accumulate(const Half<R> &h, Spinor<R> &a)
+// acc += w (h, s A_mu^dag h), the full spinor rebuilt from its upper pair.
+// w carries the boundary sign of the hop and the site scale of the input
+// (1 except for half-precision storage); it rides on fused multiply-adds.
+template <typename R> TM_HD cpx<R> fmadd(R w, cpx<R> a, cpx<R> acc) { return {acc.re + w * a.re, acc.im + w * a.im}; }
+
+template <int MU, int S, typename R> TM_HD void accumulate(const Half<R> &h, R w, Spinor<R> &a)
 {
+    const R ws = S > 0 ? w : -w;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        a[0][c] = a[0][c] + h[0][c];
-        a[1][c] = a[1][c] + h[1][c];
-        if (MU == 0) {  // A_0^dag h = (-h0, -h1)
-            a[2][c] = S > 0 ? a[2][c] - h[0][c] : a[2][c] + h[0][c];
-            a[3][c] = S > 0 ? a[3][c] - h[1][c] : a[3][c] + h[1][c];
-        } else if (MU == 1) {  // A_1^dag h = (i h1, i h0)
-            a[2][c] = S > 0 ? a[2][c] + ti(h[1][c]) : a[2][c] + tmi(h[1][c]);
-            a[3][c] = S > 0 ? a[3][c] + ti(h[0][c]) : a[3][c] + tmi(h[0][c]);
-        } else if (MU == 2) {  // A_2^dag h = (h1, -h0)
-            a[2][c] = S > 0 ? a[2][c] + h[1][c] : a[2][c] - h[1][c];
-            a[3][c] = S > 0 ? a[3][c] - h[0][c] : a[3][c] + h[0][c];
-        } else {  // A_3^dag h = (i h0, -i h1)
-            a[2][c] = S > 0 ? a[2][c] + ti(h[0][c]) : a[2][c] + tmi(h[0][c]);
-            a[3][c] = S > 0 ? a[3][c] + tmi(h[1][c]) : a[3][c] + ti(h[1][c]);
+        a[0][c] = fmadd(w, h[0][c], a[0][c]);
+        a[1][c] = fmadd(w, h[1][c], a[1][c]);
+        if (MU == 0) {  // s A_0^dag h = -s (h0, h1)
+            a[2][c] = fmadd(-ws, h[0][c], a[2][c]);
+            a[3][c] = fmadd(-ws, h[1][c], a[3][c]);
+        } else if (MU == 1) {  // s A_1^dag h = s (i h1, i h0)
+            a[2][c] = fmadd(ws, ti(h[1][c]), a[2][c]);
+            a[3][c] = fmadd(ws, ti(h[0][c]), a[3][c]);
+        } else if (MU == 2) {  // s A_2^dag h = s (h1, -h0)
+            a[2][c] = fmadd(ws, h[1][c], a[2][c]);
+            a[3][c] = fmadd(-ws, h[0][c], a[3][c]);
+        } else {  // s A_3^dag h = s (i h0, -i h1)
+            a[2][c] = fmadd(ws, ti(h[0][c]), a[2][c]);
+            a[3][c] = fmadd(-ws, ti(h[1][c]), a[3][c]);
         }
     }
 }
@@ -408,14 +443,6 @@ template <bool DAG, typename R> TM_HD void link_mul(const Link<R> &u, const Half
             for (int b = 0; b < 3; ++b) acc = DAG ? cjmadd(u[b][a], h[s][b], acc) : cmadd(u[a][b], h[s][b], acc);
             r[s][a] = acc;
         }
-}
-
-template <typename R> TM_HD void negate_half(Half<R> &h)
-{
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) h[s][c] = -h[s][c];
 }
 
 // Where the hop finds its links.  GlobalLinks reads the forward link
@@ -466,23 +493,23 @@ TM_HD void hop_dir(const Geom &g, const Nbrs &n, const Src &src, const void *in,
         Spinor<R> s;
         Half<R> h, r;
         Link<R> u;
-        SpinorIO<P>::load(in, g.vh, n.fwd[MU], s);
+        R w = SpinorIO<P>::load_raw(in, g.vh, n.fwd[MU], s);
         project<MU, SF>(s, h);
         src.template fwd<MU>(n, u);
         link_mul<false>(u, h, r);
-        if (n.wf[MU] && g.anti[MU]) negate_half(r);
-        accumulate<MU, SF>(r, acc);
+        if (n.wf[MU] && g.anti[MU]) w = -w;
+        accumulate<MU, SF>(r, w, acc);
     }
     {
         Spinor<R> s;
         Half<R> h, r;
         Link<R> u;
-        SpinorIO<P>::load(in, g.vh, n.bwd[MU], s);
+        R w = SpinorIO<P>::load_raw(in, g.vh, n.bwd[MU], s);
         project<MU, SB>(s, h);
         src.template bwd<MU>(n, u);
         link_mul<true>(u, h, r);
-        if (n.wb[MU] && g.anti[MU]) negate_half(r);
-        accumulate<MU, SB>(r, acc);
+        if (n.wb[MU] && g.anti[MU]) w = -w;
+        accumulate<MU, SB>(r, w, acc);
     }
 }
 
@@ -515,13 +542,25 @@ TM_HD void hop_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, R
 // (u = spins 0,1; l = spins 2,3).  With gamma5 = diag(1,1,-1,-1) this covers
 // the twisted-mass factors (1 +- i mut gamma5)^(+-1) and the final gamma5.
 struct Coef {
-    double au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im;
+    double d[8];  // au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im
+    float f[8];   // the same, rounded once on the host for single-precision kernels
+    Coef() = default;
+    __host__ __device__ Coef(double au_re, double au_im, double al_re, double al_im, double bu_re, double bu_im,
+                             double bl_re, double bl_im)
+        : d{au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im},
+          f{float(au_re), float(au_im), float(al_re), float(al_im), float(bu_re), float(bu_im), float(bl_re),
+            float(bl_im)}
+    {
+    }
+    TM_HD const double *vals(double) const { return d; }
+    TM_HD const float *vals(float) const { return f; }
 };
 
 template <typename R> TM_HD void epilogue(const Coef &k, const Spinor<R> &hop, const Spinor<R> *x, Spinor<R> &out)
 {
-    cpx<R> au = {R(k.au_re), R(k.au_im)}, al = {R(k.al_re), R(k.al_im)};
-    cpx<R> bu = {R(k.bu_re), R(k.bu_im)}, bl = {R(k.bl_re), R(k.bl_im)};
+    const R *v = k.vals(R(0));
+    cpx<R> au = {v[0], v[1]}, al = {v[2], v[3]};
+    cpx<R> bu = {v[4], v[5]}, bl = {v[6], v[7]};
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll

@@ -42,7 +42,7 @@ Coef coef_qtm_b(double kappa, double mut)
 
 // ------------------------------------------------------------------ hop
 template <int P, int RECON, bool DAG, bool HASX>
-__global__ void __launch_bounds__(256) k_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,
+__global__ void __launch_bounds__(128, TM_HOP_MINB(P)) k_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,
                                              const void *__restrict__ in, void *__restrict__ out,
                                              const void *__restrict__ x, Coef k)
 {

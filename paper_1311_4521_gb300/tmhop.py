@@ -73,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "tm_cg_QdagQ": ([P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
         "tm_ctx_set_autotune": ([P, I], I),
         "tm_force": ([P, P, P, P, D, D, I, P], I),
+        "tm_solve_eo": ([P, P, P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
         "tm_Qtm_batch": ([P, I, P, P, P, D, D, I, P], I),
         "tm_cg_QdagQ_batch": ([P, I, P, P, P, P, ctypes.POINTER(CgParams), P, P], I),
     }
@@ -180,6 +181,16 @@ def tm_cg_QdagQ(ctx, U_hi, U_lo, x_dev, b_dev, params: CgParams, stream=None):
     info = CgInfo()
     st = lib.tm_cg_QdagQ(ctx, U_hi, U_lo, _ptr(x_dev), _ptr(b_dev), ctypes.byref(params), ctypes.byref(info),
                          _stream(stream))
+    if st not in (TM_OK, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE):
+        _check(ctx, st)
+    return st, info
+
+
+def tm_solve_eo(ctx, U_hi, U_lo, x_e, x_o, b_e, b_o, params: CgParams, stream=None):
+    """Full-lattice solve M x = b; returns (status, CgInfo of the even-site solve)."""
+    info = CgInfo()
+    st = lib.tm_solve_eo(ctx, U_hi, U_lo, _ptr(x_e), _ptr(x_o), _ptr(b_e), _ptr(b_o), ctypes.byref(params),
+                         ctypes.byref(info), _stream(stream))
     if st not in (TM_OK, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE):
         _check(ctx, st)
     return st, info
@@ -314,6 +325,14 @@ class Context:
     def Qtm(self, U: Gauge, out, inp, kappa, mu, sign=1):
         tm_Qtm(self.handle, U.handle, out, inp, kappa, mu, sign)
         return out
+
+    def solve_eo(self, U_hi: Gauge, x_e, x_o, b_e, b_o, kappa, mu, tol=1e-10, maxiter=30000,
+                 U_lo: Gauge | None = None, reliable_every=50, use_graph=True, reliable_delta=0.1):
+        prm = CgParams(float(kappa), float(mu), float(tol), int(maxiter), int(reliable_every), int(bool(use_graph)),
+                       float(reliable_delta))
+        st, info = tm_solve_eo(self.handle, U_hi.handle, U_lo.handle if U_lo is not None else None,
+                               x_e, x_o, b_e, b_o, prm)
+        return st, info.as_dict()
 
     def force(self, U: Gauge, X_e, kappa, mu, mode=TM_FORCE_SU3) -> torch.Tensor:
         """Force (or complex gradient) of S = phi^dag (Q^dag Q)^-1 phi given packed X; (4, V, 3, 3) complex128."""
