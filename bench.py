@@ -44,7 +44,7 @@ DIMS = (32, 32, 32, 64)
 KAPPA, MU = 0.1394, 0.0015
 SAMPLE_DIMS = (16, 16, 16, 16)       # bounded sample for the CPU reference arm
 L2_BYTES = 129 * 2 ** 20
-REAL = {"f64": 8, "f32": 4, "f16": 2}
+REAL = {"f64": 8, "f64x": 8, "f32": 4, "f16": 2}
 HOP_FLOPS = 1320
 QTM_FLOPS = 2 * HOP_FLOPS + 72 + 96
 # FP64 ALU peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
@@ -55,9 +55,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # (profiles/k_hop_f64_24x24x24x48_full.md, profiles/k_hop_dram_f32_f16_32x32x32x64.md),
 # scaled to a 32^3x64 launch by the site count, valid only for the kernel
 # sources they were taken from (hash of csrc/tm_device.cuh + csrc/tm_kernels.cu).
-TRAFFIC = {"src": "5162b3846366947c",
-           "per_site": {("f64", 18): (513.5e6 + 37.4e6) / 331776, ("f32", 12): (607.6e6 + 68.7e6) / 1048576,
-                        ("f16", 12): (312.1e6 + 27.7e6) / 1048576}}
+TRAFFIC = {"src": "e6aaae868d14d441",
+           "per_site": {("f64", 18): (512679424 + 34694400) / 331776, ("f32", 12): (607374080 + 69613312) / 1048576,
+                        ("f16", 12): (312119552 + 28481280) / 1048576}}
 
 
 def kernel_source_hash() -> str:
@@ -87,6 +87,33 @@ def algo_bytes(prec: str, recon: int) -> dict:
     a = hop_bytes(prec, recon)
     b = hop_bytes(prec, recon) + reread
     return {"kernel_a": a, "kernel_b": b, "qtm": a + b}
+
+
+class Ranks:
+    """Rank bookkeeping of a replicas-only run (one process per GPU, no data
+    exchange): a barrier around timed regions and the maximum of a time over
+    ranks.  ``dist`` is torch.distributed (initialised) or None for one rank."""
+
+    def __init__(self, dist=None, device="cuda"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def allmax(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, bytes_per_unit: float, max_ms: float) -> float:
+    """Whole-job GB/s: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * bytes_per_unit / (max_ms * 1e-3) / 1e9
 
 
 def load_peaks() -> dict:
@@ -193,16 +220,8 @@ def gpu_arm(args) -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def allmax(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(dist, "cuda")
+    barrier, allmax = ranks.barrier, ranks.allmax
 
     DIMS = args.lattice
     prec, recon = args.prec, args.recon
@@ -243,7 +262,7 @@ def gpu_arm(args) -> None:
     max_ms = allmax(total_ms)
     ab = algo_bytes(prec, recon)
     ms_per_step = max_ms / args.steps
-    value = world * vh * ab["qtm"] / (ms_per_step * 1e-3) / 1e9
+    value = job_throughput(world, vh, ab["qtm"], ms_per_step)
     gflops = world * vh * QTM_FLOPS / (ms_per_step * 1e-3) / 1e9
     kb_tflops = vh * (HOP_FLOPS + 96) / (kb_ms * 1e-3) / 1e12
     kb_gbs = vh * ab["kernel_b"] / (kb_ms * 1e-3) / 1e9
@@ -301,7 +320,7 @@ def gpu_arm(args) -> None:
     # ---- storage-precision table (HBM-bound variants)
     table = {}
     if not args.no_table:
-        for tp, tr in (("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12)):
+        for tp, tr in (("f64", 12), ("f64x", 18), ("f64x", 12), ("f32", 18), ("f32", 12), ("f16", 12)):
             gp = ctx.gauge(DIMS, U, tp, tr)
             sp = ctx.pack(psi, tp)
             dp = ctx.empty(vh, tp)
@@ -384,29 +403,36 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier) -> dict:
     U = F.gauge_field(dims, F.SEED_CG_48, "near", 0.3)
     b = F.gaussian_spinor(vh, F.SEED_CG_48, 1)
     gh = ctx.gauge(dims, U, "f64", 18)
+    gx = ctx.gauge(dims, U, "f64x", 18)
     lo = {"mixed_f32": ctx.gauge(dims, U, "f32", 12), "mixed_f16": ctx.gauge(dims, U, "f16", 12)}
     del U
     bd = ctx.pack(b, "f64")
+    bx = ctx.pack(b, "f64x")
     x = ctx.empty(vh, "f64")
     out = {"lattice": list(dims), "tol": 1e-10, "kappa": KAPPA, "mu": MU, "reliable_every": 50,
            "reliable_delta": 0.1, "source": "Gaussian, seed 2013", "time": "CUDA events around one warm solve"}
     stream = torch.cuda.current_stream()
-    for name, gl in (("fp64", None), ("mixed_f32", lo["mixed_f32"]), ("mixed_f16", lo["mixed_f16"])):
+    runs = (("fp64", gh, bd, None), ("mixed_f32", gh, bd, lo["mixed_f32"]), ("mixed_f16", gh, bd, lo["mixed_f16"]),
+            ("fp64x", gx, bx, None), ("mixed_f32_fp64x", gx, bx, lo["mixed_f32"]),
+            ("mixed_f16_fp64x", gx, bx, lo["mixed_f16"]))
+    for name, ghi, bb, gl in runs:
         for rep in range(2):
             x.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             barrier()
             torch.cuda.synchronize()
             e0.record(stream)
-            st, info = ctx.cg(gh, x, bd, KAPPA, MU, 1e-10, 30000, gl, 50, True, 0.1)
+            st, info = ctx.cg(ghi, x, bb, KAPPA, MU, 1e-10, 30000, gl, 50, True, 0.1)
             e1.record(stream)
             torch.cuda.synchronize()
         sec = allmax(e0.elapsed_time(e1) / 1e3)
         out[name] = {"seconds": round(sec, 4), "iters": info["iters"], "reliable_updates": info["reliable_updates"],
                      "true_relres": info["true_relres"], "converged": st == tmhop.TM_OK}
-    for name in ("mixed_f32", "mixed_f16"):
+    for name in ("mixed_f32", "mixed_f16", "fp64x", "mixed_f32_fp64x", "mixed_f16_fp64x"):
         out[name]["speedup_vs_fp64"] = round(out["fp64"]["seconds"] / out[name]["seconds"], 2)
-    for g in [gh] + list(lo.values()):
+    out["fp64x_note"] = ("fp64x: x, b and the reliable updates in double-float storage/arithmetic (TM_F64X, "
+                         "~48-bit significand); convergence still judged on the true residual")
+    for g in [gh, gx] + list(lo.values()):
         g.close()
     return out
 
@@ -656,7 +682,7 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=DIMS,
                     help="Lx,Ly,Lz,Lt (default 32,32,32,64)")
-    ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64")
+    ap.add_argument("--prec", choices=["f64", "f64x", "f32", "f16"], default="f64")
     ap.add_argument("--recon", type=int, choices=[12, 18], default=18)
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--table-steps", type=int, default=300)

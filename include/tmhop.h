@@ -56,7 +56,11 @@ typedef enum {
     TM_ERR_UNSUPPORTED = 6     /* valid but not implemented combination */
 } tm_status;
 
-typedef enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2 } tm_prec;
+/* Storage precisions.  TM_F64X stores each FP64 value as a pair of FP32
+ * numbers (hi, lo; about 48 significant bits) and computes with double-float
+ * arithmetic on the FP32 units, which on GB300 issue 64 times as many FMAs
+ * per clock as the FP64 units; results agree with FP64 to ~1e-14. */
+typedef enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2, TM_F64X = 3 } tm_prec;
 
 enum { TM_EO = 0,   /* output even sites, input odd sites: H_eo */
        TM_OE = 1 }; /* output odd sites, input even sites: H_oe */
@@ -93,6 +97,7 @@ tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on);
  *   TM_F32:  6 arrays of Vh float4  (two components each)              96*Vh
  *   TM_F16:  3 arrays of Vh x 8 halves (four components each, scaled by
  *            the site norm) followed by Vh floats (the site norm = max |re|,|im|) 52*Vh
+ *   TM_F64X: 12 arrays of Vh float4 (re.hi, re.lo, im.hi, im.lo)       192*Vh
  * Returns 0 for an invalid prec. */
 size_t tm_spinor_bytes(long vh, int prec);
 
@@ -109,7 +114,8 @@ tm_status tm_spinor_unpack(tm_ctx *ctx, long vh, const void *in_dev, double *out
  * [4][V][3][3] (mu = 0 is time, then x, y, z; row-major 3x3).  prec is the
  * storage precision; reconstruct 18 stores all nine complex entries, 12
  * stores two rows and rebuilds the third as conj(row0 x row1), which is
- * exact for SU(3) links only (TM_F16 requires 12).  bc[mu] in {+1,-1} is
+ * exact for SU(3) links only (TM_F16 requires 12; TM_F64X stores every
+ * complex entry as a float4 of hi/lo pairs).  bc[mu] in {+1,-1} is
  * the boundary sign of direction mu.  The handle owns its device memory
  * and keeps no reference to U_dev.  Synchronous with respect to stream. */
 tm_status tm_gauge_create(tm_ctx *ctx, const int dims[4], const double *U_dev, int prec, int reconstruct,
@@ -166,9 +172,10 @@ typedef struct {
  * inversion the tmLQCD inverter performs (the paper's Sec. 3 samples it;
  * Q^dag Q = Q(-mu) Q(mu) is Hermitian positive definite for mu != 0).
  *
- * U_hi is an FP64 gauge handle; x_dev (in: initial guess, out: solution)
- * and b_dev are FP64 packed even fields.  U_lo selects the inner solver:
- * NULL or U_hi gives a plain FP64 CG, checked against the FP64 true
+ * U_hi is an FP64 or FP64X gauge handle; x_dev (in: initial guess, out:
+ * solution) and b_dev are even fields packed in U_hi's precision.  U_lo
+ * selects the inner solver: NULL, U_hi or another handle of U_hi's precision
+ * gives a plain CG in that precision, checked against the FP64 true
  * residual whenever the recursive residual reaches tol; an FP32 or FP16
  * handle gives a mixed-precision CG whose vectors are stored in that
  * precision with FP32 arithmetic; its solution increments are accumulated

@@ -31,7 +31,7 @@ tm_status cuda_fail(tm_ctx *ctx, cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
-bool valid_prec(int p) { return p == TM_F64 || p == TM_F32 || p == TM_F16; }
+bool valid_prec(int p) { return p == TM_F64 || p == TM_F32 || p == TM_F16 || p == TM_F64X; }
 
 }  // namespace
 

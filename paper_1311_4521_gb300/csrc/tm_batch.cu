@@ -5,11 +5,14 @@
 // Systems that share a gauge handle form a group.  A launch walks a work
 // list of tiles of all groups; its CTAs are persistent (each takes items
 // blockIdx.x, blockIdx.x + gridDim.x, ...), so one launch covers every
-// lattice whatever their sizes.  For a group with several right-hand sides
-// the CTA copies the 8 links of each tile site into shared memory once and
-// applies them to all right-hand sides (the links are most of the bytes of
-// a hop, so n right-hand sides cost much less than n launches); with one
-// right-hand side per group links are read straight from global memory.
+// lattice whatever their sizes.  The links are most of the bytes of a hop,
+// so a group's n right-hand sides should read them once, not n times.  Two
+// ways, both measured: (a) a CTA copies the 8 links of each tile site into
+// shared memory once and applies them to all right-hand sides in passes;
+// (b) consecutive work items are the right-hand sides of one tile, so the
+// CTAs that need the same links run back to back and share them through L2
+// (default-cached loads).  With one right-hand side per group links are
+// streamed from global memory (evict-first).
 // Tile size (right-hand sides processed together) and the number of
 // persistent CTAs are picked by timing candidates on first use.
 //
@@ -26,127 +29,9 @@
 #include <string>
 #include <vector>
 
-#include "tm_cg.cuh"
-#include "tm_internal.h"
+#include "tm_batch.cuh"
 
 namespace twm {
-
-enum Role { R_X, R_B, R_R, R_P, R_AP, R_Q, R_T, R_Y, R_AX, R_THI, R_QHI, R_IN, R_OUT, NROLE };
-
-struct BSys {
-    void *f[NROLE];
-    double *partials;  // one slot per work tile of the system's lattice
-    CgScalars *s;
-    unsigned vh;
-};
-
-struct BGroup {
-    Geom g;
-    const void *links;  // gauge storage in the launch's precision
-    int nrhs, sys0;     // systems sys0 .. sys0 + nrhs - 1
-    unsigned item0;     // first work item of the group
-    unsigned ntiles;    // tiles covering the group's Vh sites
-};
-
-constexpr int BT = 128;   // threads per CTA of the batched hop
-constexpr int BLA = 256;  // threads per CTA of the batched vector kernels
-
-__device__ __forceinline__ int find_group(const BGroup *gr, int ng, unsigned item)
-{
-    int gi = 0;
-    while (gi + 1 < ng && item >= gr[gi + 1].item0) ++gi;
-    return gi;
-}
-
-template <int P, int RECON, int NRB, bool NORM>
-__global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ groups, int ngroups, unsigned nitems,
-                                                  const BSys *__restrict__ sys, int parity, int rin, int rout, int rx,
-                                                  Coef k, int gate)
-{
-    using L = LinkIO<P, RECON>;
-    using V = typename L::V;
-    using R = typename SpinorIO<P>::R;
-    constexpr int TS = BT / NRB;
-    __shared__ V tile[NRB > 1 ? 8 * L::NCHUNK * TS : 1];
-    __shared__ unsigned bwd_idx[NRB > 1 ? 4 * TS : 1];
-    __shared__ double red[BT];
-    const unsigned tx = threadIdx.x % TS, ty = threadIdx.x / TS;
-
-    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const BGroup &G = groups[find_group(groups, ngroups, item)];
-        const unsigned rel = item - G.item0;
-        const unsigned tno = NRB == 1 ? rel % G.ntiles : rel;
-        const unsigned i = tno * TS + tx;
-        const V *links = static_cast<const V *>(G.links);
-        if (NRB > 1) {
-            // skip the tile (and its link traffic) when no system of the group is active
-            bool any = false;
-            for (int r = 0; r < G.nrhs && !any; ++r) any = !gated(sys[G.sys0 + r].s, gate);
-            if (!any) continue;   // uniform over the block
-            __syncthreads();  // readers of the previous tile are done
-            if (ty == 0) {
-                unsigned site = tno * TS + tx;
-                if (site < G.g.vh) {
-                    Nbrs n;
-                    neighbours(G.g, parity, site, n);
-                    for (int m = 0; m < 4; ++m) bwd_idx[m * TS + tx] = n.bwd[m];
-                }
-            }
-            __syncthreads();
-            for (unsigned e = threadIdx.x; e < 8u * L::NCHUNK * TS; e += BT) {
-                const unsigned s = e % TS, dc = e / TS, c = dc % L::NCHUNK, d = dc / L::NCHUNK;
-                const unsigned site = tno * TS + s;
-                V v{};
-                if (site < G.g.vh) {
-                    const unsigned idx = d < 4 ? site : bwd_idx[(d - 4) * TS + s];
-                    const unsigned blk = d < 4 ? 4 * parity + d : 4 * (1 - parity) + (d - 4);
-                    v = ld_stream(links + (size_t(blk) * L::NCHUNK + c) * G.g.vh + idx);
-                }
-                tile[e] = v;
-            }
-            __syncthreads();
-        }
-        const int passes = NRB == 1 ? 1 : (G.nrhs + NRB - 1) / NRB;
-        for (int q = 0; q < passes; ++q) {
-            const int r = NRB == 1 ? int(rel / G.ntiles) : q * NRB + int(ty);
-            const BSys *S = r < G.nrhs ? &sys[G.sys0 + r] : nullptr;
-            const bool active = S && !gated(S->s, gate);
-            double nrm = 0.0;
-            if (active && i < G.g.vh) {
-                Spinor<R> acc, o;
-                Nbrs n;
-                neighbours(G.g, parity, i, n);
-                if (NRB > 1) {
-                    StagedLinks<P, RECON> src{tile, TS, tx};
-                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
-                } else {
-                    GlobalLinks<P, RECON> src{links, G.g.vh, i, parity};
-                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
-                }
-                if (rx >= 0) {
-                    Spinor<R> xs;
-                    SpinorIO<P>::load(S->f[rx], G.g.vh, i, xs);
-                    epilogue(k, acc, &xs, o);
-                } else {
-                    epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
-                }
-                SpinorIO<P>::store(S->f[rout], G.g.vh, i, o);
-                if (NORM) nrm = norm2(o);
-            }
-            if (NORM) {
-                // one partial per (system, tile): the TS threads of each right-hand side, summed in order
-                red[threadIdx.x] = nrm;
-                __syncthreads();
-                if (tx == 0 && active) {
-                    double sum = 0.0;
-                    for (int t = 0; t < TS; ++t) sum += red[ty * TS + t];
-                    S->partials[tno] = sum;
-                }
-                __syncthreads();
-            }
-        }
-    }
-}
 
 // Maps a vector-kernel item to (system, tile of BLA sites) by the prefix table item0[nsys+1].
 __device__ __forceinline__ int find_sys(const unsigned *item0, int nsys, unsigned item)
@@ -185,8 +70,8 @@ __global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_update(const BS
         const unsigned tno = item - item0[k], i = tno * BLA + threadIdx.x;
         double nrm = 0.0;
         if (i < S.vh) {
-            const R a = R(S.s->alpha);
-            const RY ay = RY(S.s->alpha);
+            const R a = to_R<R>(S.s->alpha);
+            const RY ay = to_R<RY>(S.s->alpha);
             Spinor<R> pv, av, rv;
             Spinor<RY> yv;
             SpinorIO<P>::load(S.f[R_P], S.vh, i, pv);
@@ -226,7 +111,7 @@ __global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_pupdate(const B
         Spinor<R> rv, pv;
         SpinorIO<P>::load(S.f[R_R], S.vh, i, rv);
         if (!restart) {
-            const R b = R(S.s->rr_new / S.s->rr);
+            const R b = to_R<R>(S.s->rr_new / S.s->rr);
             SpinorIO<P>::load(S.f[R_P], S.vh, i, pv);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
@@ -293,7 +178,7 @@ __global__ void __launch_bounds__(BLA, 3) k_batch_residual(const BSys *__restric
                 for (int c = 0; c < 3; ++c) {
                     bv[sp][c].re -= av[sp][c].re;
                     bv[sp][c].im -= av[sp][c].im;
-                    lo[sp][c] = {R(bv[sp][c].re), R(bv[sp][c].im)};
+                    lo[sp][c] = {to_R<R>(bv[sp][c].re), to_R<R>(bv[sp][c].im)};
                 }
             SpinorIO<P>::store(S.f[R_R], S.vh, i, lo);
             nrm = norm2(bv);
@@ -360,14 +245,6 @@ __global__ void __launch_bounds__(BLA, 4) k_batch_finish(const BSys *__restrict_
 // ------------------------------------------------------------------ host side
 namespace {
 
-struct HopTable {
-    int nrb = 1;            // right-hand sides per pass (1: no link staging)
-    unsigned grid = 0;      // persistent CTAs
-    unsigned nitems = 0;
-    BGroup *dev = nullptr;  // device copy of the groups
-    int ngroups = 0;
-};
-
 struct Batch {
     int nsys = 0, ngroups = 0;
     int P = F64, recon_lo = 18, recon_hi = 18, PY = F64;
@@ -381,55 +258,28 @@ struct Batch {
 
 unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
 
-template <int P, int RECON, int NRB>
-cudaError_t hop_nrb(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
-                    int gate, cudaStream_t st)
-{
-    if (norm)
-        k_batch_hop<P, RECON, NRB, true><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
-    else
-        k_batch_hop<P, RECON, NRB, false><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
-    return cudaGetLastError();
-}
-
-template <int P, int RECON>
-cudaError_t hop_pr(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
-                   int gate, cudaStream_t st)
-{
-    switch (t.nrb) {
-    case 1: return hop_nrb<P, RECON, 1>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case 2:
-        // FP64 tiles of 64 sites would exceed 48 KB of static shared memory
-        if constexpr (P != F64) return hop_nrb<P, RECON, 2>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-        return cudaErrorInvalidValue;
-    case 4: return hop_nrb<P, RECON, 4>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case 8: return hop_nrb<P, RECON, 8>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    }
-    return cudaErrorInvalidValue;
-}
-
 cudaError_t bhop(int prec, int recon, const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx,
                  const Coef &k, bool norm, int gate, cudaStream_t st)
 {
     if (t.nitems == 0) return cudaSuccess;
     switch (prec * 100 + recon) {
-    case F64 * 100 + 18: return hop_pr<F64, 18>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F64 * 100 + 12: return hop_pr<F64, 12>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F32 * 100 + 18: return hop_pr<F32, 18>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F32 * 100 + 12: return hop_pr<F32, 12>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F16 * 100 + 12: return hop_pr<F16, 12>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F64 * 100 + 18: return batch_hop_f64(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F64X * 100 + 18: return batch_hop_f64x(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F32 * 100 + 12: return batch_hop_f32_12(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F32 * 100 + 18: return batch_hop_f32_18(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F16 * 100 + 12: return batch_hop_f16(t, sys, parity, rin, rout, rx, k, norm, gate, st);
     }
     return cudaErrorInvalidValue;
 }
 
-// Valid right-hand-side pass widths for a storage format (static shared memory <= 48 KB).
+// Candidate link-sharing modes for a storage format (static shared memory <= 48 KB).
 std::vector<int> nrb_candidates(int prec, int recon, int nrhs_max)
 {
     std::vector<int> c{1};
     if (nrhs_max <= 1) return c;
-    if (prec != F64) c.push_back(2);
+    c.push_back(0);
+    if (prec != F64 && prec != F64X) c.push_back(2);
     c.push_back(4);
-    c.push_back(8);
     (void)recon;
     return c;
 }
@@ -439,12 +289,12 @@ cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_
                         cudaStream_t st, std::vector<BGroup> &host)
 {
     host = tmpl;
-    const unsigned ts = BT / nrb;
+    const unsigned ts = nrb > 1 ? BT / nrb : BT;
     unsigned item = 0;
     for (auto &g : host) {
         g.item0 = item;
         g.ntiles = cdiv(g.g.vh, ts);
-        item += nrb == 1 ? g.ntiles * unsigned(g.nrhs) : g.ntiles;
+        item += nrb <= 1 ? g.ntiles * unsigned(g.nrhs) : g.ntiles;
     }
     t.nrb = nrb;
     t.nitems = item;
@@ -663,6 +513,8 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
     for (size_t g = 0; g < handles.size(); ++g)
         if (lo[g]->prec != lo[0]->prec || lo[g]->recon != lo[0]->recon || handles[g]->recon != handles[0]->recon)
             return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_cg_QdagQ_batch: all systems need the same storage formats");
+    if (lo[0]->prec == TM_F64X)
+        return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_cg_QdagQ_batch: TM_F64X inner handles are not supported");
 
     Batch B;
     B.nsys = nsys;
@@ -760,7 +612,7 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
         k_batch_finish<<<nsys, BLA, 0, q>>>(SY, nsys, tile_sites, op, gate);
         return cudaGetLastError();
     };
-    auto hop_tile = [&](const HopTable &t) { return unsigned(BT / t.nrb); };
+    auto hop_tile = [&](const HopTable &t) { return unsigned(t.nrb > 1 ? BT / t.nrb : BT); };
     // ax = Q^dag Q x in FP64 for the systems the gate lets through
     auto qdagq_hi = [&](int gate, cudaStream_t q) {
         cudaError_t r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_X, R_THI, -1, coef_qtm_a(mut), false, gate, q);

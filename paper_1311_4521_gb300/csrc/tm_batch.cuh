@@ -1,0 +1,181 @@
+// tm_batch.cuh -- shared definitions of the batched operator and solver:
+// the system and group tables, the batched hop kernel and its launchers.
+#pragma once
+
+#include "tm_cg.cuh"
+#include "tm_internal.h"
+
+namespace twm {
+
+enum Role { R_X, R_B, R_R, R_P, R_AP, R_Q, R_T, R_Y, R_AX, R_THI, R_QHI, R_IN, R_OUT, NROLE };
+
+struct BSys {
+    void *f[NROLE];
+    double *partials;  // one slot per work tile of the system's lattice
+    CgScalars *s;
+    unsigned vh;
+};
+
+struct BGroup {
+    Geom g;
+    const void *links;  // gauge storage in the launch's precision
+    int nrhs, sys0;     // systems sys0 .. sys0 + nrhs - 1
+    unsigned item0;     // first work item of the group
+    unsigned ntiles;    // tiles covering the group's Vh sites
+};
+
+constexpr int BT = 128;   // threads per CTA of the batched hop
+constexpr int BLA = 256;  // threads per CTA of the batched vector kernels
+
+__device__ __forceinline__ int find_group(const BGroup *gr, int ng, unsigned item)
+{
+    int gi = 0;
+    while (gi + 1 < ng && item >= gr[gi + 1].item0) ++gi;
+    return gi;
+}
+
+
+struct HopTable {
+    int nrb = 1;            // right-hand sides per pass (1: no link staging)
+    unsigned grid = 0;      // persistent CTAs
+    unsigned nitems = 0;
+    BGroup *dev = nullptr;  // device copy of the groups
+    int ngroups = 0;
+};
+
+// Launches of the batched hop for one storage format (tm_batch_hop_*.cu).
+cudaError_t batch_hop_f64(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
+                          bool norm, int gate, cudaStream_t st);
+cudaError_t batch_hop_f64x(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
+                           bool norm, int gate, cudaStream_t st);
+cudaError_t batch_hop_f32_12(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
+                             bool norm, int gate, cudaStream_t st);
+cudaError_t batch_hop_f32_18(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
+                             bool norm, int gate, cudaStream_t st);
+cudaError_t batch_hop_f16(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
+                          bool norm, int gate, cudaStream_t st);
+
+// NRB: 1 streams links, items (tile, rhs) with the right-hand side fastest;
+// 0 the same with default-cached links (L2 sharing); >= 2 stages the tile's
+// links in shared memory and sweeps the right-hand sides NRB at a time.
+template <int P, int RECON, int NRB, bool NORM>
+__global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ groups, int ngroups, unsigned nitems,
+                                                  const BSys *__restrict__ sys, int parity, int rin, int rout, int rx,
+                                                  Coef k, int gate)
+{
+    using L = LinkIO<P, RECON>;
+    using V = typename L::V;
+    using R = typename SpinorIO<P>::R;
+    constexpr int TS = NRB > 1 ? BT / NRB : BT;
+    __shared__ V tile[NRB > 1 ? 8 * L::NCHUNK * TS : 1];
+    __shared__ unsigned bwd_idx[NRB > 1 ? 4 * TS : 1];
+    __shared__ double red[BT];
+    const unsigned tx = threadIdx.x % TS, ty = threadIdx.x / TS;
+
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const BGroup &G = groups[find_group(groups, ngroups, item)];
+        const unsigned rel = item - G.item0;
+        const unsigned tno = NRB <= 1 ? rel / unsigned(G.nrhs) : rel;
+        const unsigned i = tno * TS + tx;
+        const V *links = static_cast<const V *>(G.links);
+        if (NRB > 1) {
+            // skip the tile (and its link traffic) when no system of the group is active
+            bool any = false;
+            for (int r = 0; r < G.nrhs && !any; ++r) any = !gated(sys[G.sys0 + r].s, gate);
+            if (!any) continue;   // uniform over the block
+            __syncthreads();  // readers of the previous tile are done
+            if (ty == 0) {
+                unsigned site = tno * TS + tx;
+                if (site < G.g.vh) {
+                    Nbrs n;
+                    neighbours(G.g, parity, site, n);
+                    for (int m = 0; m < 4; ++m) bwd_idx[m * TS + tx] = n.bwd[m];
+                }
+            }
+            __syncthreads();
+            for (unsigned e = threadIdx.x; e < 8u * L::NCHUNK * TS; e += BT) {
+                const unsigned s = e % TS, dc = e / TS, c = dc % L::NCHUNK, d = dc / L::NCHUNK;
+                const unsigned site = tno * TS + s;
+                V v{};
+                if (site < G.g.vh) {
+                    const unsigned idx = d < 4 ? site : bwd_idx[(d - 4) * TS + s];
+                    const unsigned blk = d < 4 ? 4 * parity + d : 4 * (1 - parity) + (d - 4);
+                    v = ld_stream(links + (size_t(blk) * L::NCHUNK + c) * G.g.vh + idx);
+                }
+                tile[e] = v;
+            }
+            __syncthreads();
+        }
+        const int passes = NRB <= 1 ? 1 : (G.nrhs + NRB - 1) / NRB;
+        for (int q = 0; q < passes; ++q) {
+            const int r = NRB <= 1 ? int(rel % unsigned(G.nrhs)) : q * NRB + int(ty);
+            const BSys *S = r < G.nrhs ? &sys[G.sys0 + r] : nullptr;
+            const bool active = S && !gated(S->s, gate);
+            double nrm = 0.0;
+            if (active && i < G.g.vh) {
+                Spinor<R> acc, o;
+                Nbrs n;
+                neighbours(G.g, parity, i, n);
+                if (NRB > 1) {
+                    StagedLinks<P, RECON> src{tile, TS, tx};
+                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
+                } else {
+                    GlobalLinks<P, RECON, NRB == 1> src{links, G.g.vh, i, parity};
+                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
+                }
+                if (rx >= 0) {
+                    Spinor<R> xs;
+                    SpinorIO<P>::load(S->f[rx], G.g.vh, i, xs);
+                    epilogue(k, acc, &xs, o);
+                } else {
+                    epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
+                }
+                SpinorIO<P>::store(S->f[rout], G.g.vh, i, o);
+                if (NORM) nrm = norm2(o);
+            }
+            if (NORM) {
+                // one partial per (system, tile): the TS threads of each right-hand side, summed in order
+                red[threadIdx.x] = nrm;
+                __syncthreads();
+                if (tx == 0 && active) {
+                    double sum = 0.0;
+                    for (int t = 0; t < TS; ++t) sum += red[ty * TS + t];
+                    S->partials[tno] = sum;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+template <int P, int RECON, int NRB, bool WITH_NORM = true>
+inline cudaError_t hop_nrb(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
+                    int gate, cudaStream_t st)
+{
+    if (norm) {
+        if constexpr (WITH_NORM)
+            k_batch_hop<P, RECON, NRB, true><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+        else
+            return cudaErrorInvalidValue;
+    } else
+        k_batch_hop<P, RECON, NRB, false><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+    return cudaGetLastError();
+}
+
+template <int P, int RECON, bool WITH_NORM = true>
+inline cudaError_t hop_pr(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
+                   int gate, cudaStream_t st)
+{
+    switch (t.nrb) {
+    case 0: return hop_nrb<P, RECON, 0, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case 1: return hop_nrb<P, RECON, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case 2:
+        // 8-byte-per-real tiles of 64 sites would exceed 48 KB of static shared memory
+        if constexpr (P != F64 && P != F64X) return hop_nrb<P, RECON, 2, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+        return cudaErrorInvalidValue;
+    case 4: return hop_nrb<P, RECON, 4, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace twm

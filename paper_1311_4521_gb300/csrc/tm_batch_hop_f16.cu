@@ -1,0 +1,13 @@
+// tm_batch_hop_f16.cu -- the batched hop for F16-12 storage (one
+// translation unit per storage format so that they compile in parallel).
+#include "tm_batch.cuh"
+
+namespace twm {
+
+cudaError_t batch_hop_f16(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
+                        bool norm, int gate, cudaStream_t st)
+{
+    return hop_pr<F16, 12>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+}
+
+}  // namespace twm

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(HOP_BLOCK, TM_HOP_MINB(P)) k_cg_hop(Geom g, in
 
 // y += alpha p, r -= alpha Ap, rr_new = |r|^2 (y in precision PY).
 template <int P, int PY>
-__global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_update(unsigned vh, void *y, void *r, const void *p, const void *Ap,
+__global__ void __launch_bounds__(LA_BLOCK, (P == F64 || P == F64X) ? 3 : 4) k_cg_update(unsigned vh, void *y, void *r, const void *p, const void *Ap,
                                                         double *partials, CgScalars *s)
 {
     using R = typename SpinorIO<P>::R;
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_update(unsign
         SpinorIO<P>::load(Ap, vh, i, av);
         SpinorIO<P>::load(r, vh, i, rv);
         SpinorIO<PY>::load(y, vh, i, yv);
-        const R a = R(alpha);
-        const RY ay = RY(alpha);
+        const R a = to_R<R>(alpha);
+        const RY ay = to_R<RY>(alpha);
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_update(unsign
 
 // p = r + beta p with beta = rr_new / rr (restart: p = r); then rr = rr_new.
 template <int P>
-__global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_pupdate(unsigned vh, void *p, const void *r, double *partials,
+__global__ void __launch_bounds__(LA_BLOCK, (P == F64 || P == F64X) ? 3 : 4) k_cg_pupdate(unsigned vh, void *p, const void *r, double *partials,
                                                          CgScalars *s, int skip, int restart)
 {
     using R = typename SpinorIO<P>::R;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_pupdate(unsig
         SpinorIO<P>::load(r, vh, i, rv);
         if (!restart) {
             SpinorIO<P>::load(p, vh, i, pv);
-            const R b = R(beta);
+            const R b = to_R<R>(beta);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
@@ -162,43 +162,45 @@ __global__ void __launch_bounds__(LA_BLOCK, P == F64 ? 3 : 4) k_cg_pupdate(unsig
     reduce_finish<LA_BLOCK>(0.0, partials, s, FIN_ROLL);
 }
 
-// x += y (FP64), y = 0.
-template <int PY>
+// x += y (x in the high precision PH), y = 0.
+template <int PH, int PY>
 __global__ void __launch_bounds__(LA_BLOCK, 4) k_cg_accum(unsigned vh, void *x, void *y, const CgScalars *s, int gate)
 {
+    using RH = typename SpinorIO<PH>::R;
     using RY = typename SpinorIO<PY>::R;
     if (gated(s, gate)) return;
     unsigned i = blockIdx.x * LA_BLOCK + threadIdx.x;
     if (i >= vh) return;
-    Spinor<double> xv;
+    Spinor<RH> xv;
     Spinor<RY> yv, z;
-    SpinorIO<F64>::load(x, vh, i, xv);
+    SpinorIO<PH>::load(x, vh, i, xv);
     SpinorIO<PY>::load(y, vh, i, yv);
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            xv[sp][c].re += double(yv[sp][c].re);
-            xv[sp][c].im += double(yv[sp][c].im);
+            xv[sp][c].re += cvt<RH>(yv[sp][c].re);
+            xv[sp][c].im += cvt<RH>(yv[sp][c].im);
             z[sp][c] = {RY(0), RY(0)};
         }
-    SpinorIO<F64>::store(x, vh, i, xv);
+    SpinorIO<PH>::store(x, vh, i, xv);
     SpinorIO<PY>::store(y, vh, i, z);
 }
 
-// res = b - Ax (FP64, may alias Ax); r_lo = res in precision P if given; |res|^2 -> op.
-template <int P>
+// res = b - Ax (high precision PH, may alias Ax); r_lo = res in precision P if given; |res|^2 -> op.
+template <int PH, int P>
 __global__ void __launch_bounds__(LA_BLOCK, 3) k_cg_residual(unsigned vh, const void *b, const void *Ax, void *res,
-                                                          void *r_lo, double *partials, CgScalars *s, int op, int gate)
+                                                             void *r_lo, double *partials, CgScalars *s, int op, int gate)
 {
+    using RH = typename SpinorIO<PH>::R;
     using R = typename SpinorIO<P>::R;
     if (gated(s, gate)) return;
     unsigned i = blockIdx.x * LA_BLOCK + threadIdx.x;
     double nrm = 0.0;
     if (i < vh) {
-        Spinor<double> bv, av;
-        SpinorIO<F64>::load(b, vh, i, bv);
-        SpinorIO<F64>::load(Ax, vh, i, av);
+        Spinor<RH> bv, av;
+        SpinorIO<PH>::load(b, vh, i, bv);
+        SpinorIO<PH>::load(Ax, vh, i, av);
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
@@ -206,13 +208,13 @@ __global__ void __launch_bounds__(LA_BLOCK, 3) k_cg_residual(unsigned vh, const 
                 bv[sp][c].re -= av[sp][c].re;
                 bv[sp][c].im -= av[sp][c].im;
             }
-        if (res) SpinorIO<F64>::store(res, vh, i, bv);
+        if (res) SpinorIO<PH>::store(res, vh, i, bv);
         if (r_lo) {
             Spinor<R> lo;
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) lo[sp][c] = {R(bv[sp][c].re), R(bv[sp][c].im)};
+                for (int c = 0; c < 3; ++c) lo[sp][c] = {cvt<R>(bv[sp][c].re), cvt<R>(bv[sp][c].im)};
             SpinorIO<P>::store(r_lo, vh, i, lo);
         }
         nrm = norm2(bv);
@@ -220,14 +222,15 @@ __global__ void __launch_bounds__(LA_BLOCK, 3) k_cg_residual(unsigned vh, const 
     reduce_finish<LA_BLOCK>(nrm, partials, s, op);
 }
 
-// |v|^2 of an FP64 field -> op.
+// |v|^2 of a high-precision field -> op.
+template <int PH>
 __global__ void __launch_bounds__(LA_BLOCK, 4) k_cg_norm(unsigned vh, const void *v, double *partials, CgScalars *s, int op)
 {
     unsigned i = blockIdx.x * LA_BLOCK + threadIdx.x;
     double nrm = 0.0;
     if (i < vh) {
-        Spinor<double> a;
-        SpinorIO<F64>::load(v, vh, i, a);
+        Spinor<typename SpinorIO<PH>::R> a;
+        SpinorIO<PH>::load(v, vh, i, a);
         nrm = norm2(a);
     }
     reduce_finish<LA_BLOCK>(nrm, partials, s, op);
@@ -252,6 +255,7 @@ namespace {
 
 struct Work {
     unsigned vh;
+    int PH;             // high precision of x, b and the true residual (F64 or F64X)
     int P, PY;          // inner storage precision, solution-increment precision
     bool mixed;
     // FP64 fields
@@ -287,6 +291,8 @@ cudaError_t hop(const tm_gauge *U, int parity, const void *in, void *out, const 
     case F32 * 100 + 18: return hop_launch<F32, 18>(U, parity, in, out, x, k, norm, w, gate, st);
     case F32 * 100 + 12: return hop_launch<F32, 12>(U, parity, in, out, x, k, norm, w, gate, st);
     case F16 * 100 + 12: return hop_launch<F16, 12>(U, parity, in, out, x, k, norm, w, gate, st);
+    case F64X * 100 + 18: return hop_launch<F64X, 18>(U, parity, in, out, x, k, norm, w, gate, st);
+    case F64X * 100 + 12: return hop_launch<F64X, 12>(U, parity, in, out, x, k, norm, w, gate, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -313,6 +319,7 @@ cudaError_t update(const Work &w, cudaStream_t st)
 cudaError_t update_any(const Work &w, cudaStream_t st)
 {
     if (w.P == F64) return update<F64, F64>(w, st);
+    if (w.P == F64X) return update<F64X, F64X>(w, st);
     if (w.P == F32) return update<F32, F32>(w, st);
     return update<F16, F32>(w, st);
 }
@@ -321,27 +328,38 @@ cudaError_t pupdate(const Work &w, int skip, int restart, cudaStream_t st)
 {
     unsigned g = blocks(w.vh, LA_BLOCK);
     if (w.P == F64) k_cg_pupdate<F64><<<g, LA_BLOCK, 0, st>>>(w.vh, w.p, w.r, w.partials, w.s, skip, restart);
+    else if (w.P == F64X) k_cg_pupdate<F64X><<<g, LA_BLOCK, 0, st>>>(w.vh, w.p, w.r, w.partials, w.s, skip, restart);
     else if (w.P == F32) k_cg_pupdate<F32><<<g, LA_BLOCK, 0, st>>>(w.vh, w.p, w.r, w.partials, w.s, skip, restart);
     else k_cg_pupdate<F16><<<g, LA_BLOCK, 0, st>>>(w.vh, w.p, w.r, w.partials, w.s, skip, restart);
     return cudaGetLastError();
 }
 
-cudaError_t residual(const Work &w, void *res, void *r_lo, int op, int gate, cudaStream_t st)
+template <int PH>
+cudaError_t residual_h(const Work &w, void *res, void *r_lo, int op, int gate, cudaStream_t st)
 {
     unsigned g = blocks(w.vh, LA_BLOCK);
-    if (!r_lo || w.P == F64)
-        k_cg_residual<F64><<<g, LA_BLOCK, 0, st>>>(w.vh, w.b, w.ax, res, r_lo, w.partials, w.s, op, gate);
-    else if (w.P == F32)
-        k_cg_residual<F32><<<g, LA_BLOCK, 0, st>>>(w.vh, w.b, w.ax, res, r_lo, w.partials, w.s, op, gate);
+    const int P = r_lo ? w.P : PH;
+    if (P == PH)
+        k_cg_residual<PH, PH><<<g, LA_BLOCK, 0, st>>>(w.vh, w.b, w.ax, res, r_lo, w.partials, w.s, op, gate);
+    else if (P == F32)
+        k_cg_residual<PH, F32><<<g, LA_BLOCK, 0, st>>>(w.vh, w.b, w.ax, res, r_lo, w.partials, w.s, op, gate);
+    else if (P == F16)
+        k_cg_residual<PH, F16><<<g, LA_BLOCK, 0, st>>>(w.vh, w.b, w.ax, res, r_lo, w.partials, w.s, op, gate);
     else
-        k_cg_residual<F16><<<g, LA_BLOCK, 0, st>>>(w.vh, w.b, w.ax, res, r_lo, w.partials, w.s, op, gate);
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
+}
+
+cudaError_t residual(const Work &w, void *res, void *r_lo, int op, int gate, cudaStream_t st)
+{
+    return w.PH == F64X ? residual_h<F64X>(w, res, r_lo, op, gate, st) : residual_h<F64>(w, res, r_lo, op, gate, st);
 }
 
 cudaError_t zero(unsigned vh, int P, void *v, cudaStream_t st)
 {
     unsigned g = blocks(vh, LA_BLOCK);
     if (P == F64) k_cg_zero<F64><<<g, LA_BLOCK, 0, st>>>(vh, v);
+    else if (P == F64X) k_cg_zero<F64X><<<g, LA_BLOCK, 0, st>>>(vh, v);
     else if (P == F32) k_cg_zero<F32><<<g, LA_BLOCK, 0, st>>>(vh, v);
     else k_cg_zero<F16><<<g, LA_BLOCK, 0, st>>>(vh, v);
     return cudaGetLastError();
@@ -350,8 +368,8 @@ cudaError_t zero(unsigned vh, int P, void *v, cudaStream_t st)
 cudaError_t accum(const Work &w, int gate, cudaStream_t st)
 {
     unsigned g = blocks(w.vh, LA_BLOCK);
-    if (w.PY == F64) k_cg_accum<F64><<<g, LA_BLOCK, 0, st>>>(w.vh, w.x, w.y, w.s, gate);
-    else k_cg_accum<F32><<<g, LA_BLOCK, 0, st>>>(w.vh, w.x, w.y, w.s, gate);
+    if (w.PH == F64X) k_cg_accum<F64X, F32><<<g, LA_BLOCK, 0, st>>>(w.vh, w.x, w.y, w.s, gate);
+    else k_cg_accum<F64, F32><<<g, LA_BLOCK, 0, st>>>(w.vh, w.x, w.y, w.s, gate);
     return cudaGetLastError();
 }
 
@@ -431,7 +449,8 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     auto t_start = std::chrono::steady_clock::now();
     if (!ctx) return TM_ERR_ARG;
     if (!U_hi || !x_dev || !b_dev || !prm) return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: null pointer");
-    if (U_hi->prec != TM_F64) return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi must be an FP64 handle");
+    if (U_hi->prec != TM_F64 && U_hi->prec != TM_F64X)
+        return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi must be an FP64 or FP64X handle");
     if (!U_lo) U_lo = U_hi;
     if (memcmp(U_lo->dims, U_hi->dims, sizeof U_hi->dims) || memcmp(U_lo->bc, U_hi->bc, sizeof U_hi->bc))
         return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi and U_lo describe different lattices");
@@ -448,13 +467,14 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     S.mu = prm->mu;
     Work &w = S.w;
     w.vh = U_hi->geom.vh;
-    w.mixed = U_lo->prec != TM_F64;
-    w.P = w.mixed ? U_lo->prec : F64;
+    w.PH = U_hi->prec;
+    w.mixed = U_lo->prec == TM_F32 || U_lo->prec == TM_F16;
+    w.P = w.mixed ? U_lo->prec : w.PH;
     w.PY = w.P == F16 ? F32 : w.P;
     if (!w.mixed) S.Ul = U_hi;
 
     // workspace: FP64 ax, t_hi, q_hi (+ r in plain mode), inner r, p, Ap, q, t, y, partials, scalars
-    const size_t f64 = spinor_bytes(w.vh, F64), flo = spinor_bytes(w.vh, w.P), fy = spinor_bytes(w.vh, w.PY);
+    const size_t f64 = spinor_bytes(w.vh, w.PH), flo = spinor_bytes(w.vh, w.P), fy = spinor_bytes(w.vh, w.PY);
     auto al = [](size_t n) { return (n + 255) & ~size_t(255); };
     const size_t nblk = blocks(w.vh, 128) + 1;
     size_t need = 3 * al(f64) + 5 * al(flo) + (w.mixed ? al(fy) : 0) + al(nblk * sizeof(double)) + al(sizeof(CgScalars));
@@ -489,7 +509,8 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     cudaError_t e = cudaMemcpyAsync(w.s, &h, sizeof h, cudaMemcpyHostToDevice, s);
     // |b|^2, then r = b - Q^dag Q x in FP64 (the inner residual r is its rounded copy)
     if (e == cudaSuccess) {
-        k_cg_norm<<<blocks(w.vh, LA_BLOCK), LA_BLOCK, 0, s>>>(w.vh, w.b, w.partials, w.s, FIN_BB);
+        if (w.PH == F64X) k_cg_norm<F64X><<<blocks(w.vh, LA_BLOCK), LA_BLOCK, 0, s>>>(w.vh, w.b, w.partials, w.s, FIN_BB);
+        else k_cg_norm<F64><<<blocks(w.vh, LA_BLOCK), LA_BLOCK, 0, s>>>(w.vh, w.b, w.partials, w.s, FIN_BB);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = S.true_residual(nullptr, w.r, FIN_RR_TRUE, s);

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tm_dd.cuh"
+
 #define TM_HD __host__ __device__ __forceinline__
 
 // Resident CTAs per SM the hop kernels are compiled for (registers per
@@ -37,11 +39,26 @@
 #ifndef TM_HOP_MINB_F16
 #define TM_HOP_MINB_F16 5
 #endif
-#define TM_HOP_MINB(P) ((P) == 0 ? 2 : (P) == 1 ? TM_HOP_MINB_F32 : TM_HOP_MINB_F16)
+#define TM_HOP_MINB(P) ((P) == 0 || (P) == 3 ? 2 : (P) == 1 ? TM_HOP_MINB_F32 : TM_HOP_MINB_F16)
 
 namespace twm {
 
-enum { F64 = 0, F32 = 1, F16 = 2 };
+// Storage precisions: FP64; FP32; FP16 with a per-site norm; F64X, each
+// FP64 value stored as a double-float pair (FP32 hi, lo) and computed on with
+// double-float arithmetic (tm_dd.cuh).
+enum { F64 = 0, F32 = 1, F16 = 2, F64X = 3 };
+
+// Conversions between double and the compute type of a storage precision.
+template <typename R> TM_HD R to_R(double x) { return R(x); }
+template <> TM_HD dd to_R<dd>(double x) { return dd_from_double(x); }
+
+// Conversion between compute types (double, float, double-float).
+template <typename To> TM_HD To cvt(double x) { return to_R<To>(x); }
+template <typename To> TM_HD To cvt(float x) { return To(x); }
+template <typename To> TM_HD To cvt(dd x);
+template <> TM_HD dd cvt<dd>(dd x) { return x; }
+template <> TM_HD double cvt<double>(dd x) { return double(x); }
+template <> TM_HD float cvt<float>(dd x) { return x.hi; }
 
 // ---------------------------------------------------------------- complex
 template <typename R>
@@ -260,10 +277,39 @@ template <> struct SpinorIO<F16> {
     }
 };
 
+// Double-float storage: 12 arrays of Vh float4 = (re.hi, re.lo, im.hi, im.lo).
+template <> struct SpinorIO<F64X> {
+    using R = dd;
+    TM_HD static R load_raw(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        load(base, vh, i, s);
+        return R(1.f);
+    }
+    TM_HD static void load(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        const float4 *b = static_cast<const float4 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            float4 v = ld_keep(b + size_t(c) * vh + i);
+            s[c / 3][c % 3] = {dd{v.x, v.y}, dd{v.z, v.w}};
+        }
+    }
+    TM_HD static void store(void *base, unsigned vh, unsigned i, const Spinor<R> &s)
+    {
+        float4 *b = static_cast<float4 *>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const cpx<R> &a = s[c / 3][c % 3];
+            st_stream(b + size_t(c) * vh + i, make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo));
+        }
+    }
+};
+
 // Bytes of one packed parity field.
 TM_HD size_t spinor_bytes(unsigned vh, int prec)
 {
-    return prec == F64 ? size_t(192) * vh : prec == F32 ? size_t(96) * vh : prec == F16 ? size_t(52) * vh : 0;
+    return prec == F64 || prec == F64X ? size_t(192) * vh : prec == F32 ? size_t(96) * vh
+                                        : prec == F16 ? size_t(52) * vh : 0;
 }
 
 // Link storage: for each origin parity p and direction mu a block of NCHUNK
@@ -381,6 +427,50 @@ template <> struct LinkIO<F16, 12> {
     }
 };
 
+// Double-float links: each complex entry one float4 (re.hi, re.lo, im.hi, im.lo).
+template <> struct LinkIO<F64X, 18> {
+    using R = dd;
+    using V = float4;
+    static constexpr int NCHUNK = 9;
+    template <bool STREAM = true> TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            V v = ld_link<STREAM>(blk + size_t(k) * vh + i);
+            u[k / 3][k % 3] = {dd{v.x, v.y}, dd{v.z, v.w}};
+        }
+    }
+    TM_HD static void store(V *blk, unsigned vh, unsigned i, const double *m)
+    {
+        for (int k = 0; k < 9; ++k) {
+            dd re = dd_from_double(m[2 * k]), im = dd_from_double(m[2 * k + 1]);
+            blk[size_t(k) * vh + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+};
+
+template <> struct LinkIO<F64X, 12> {
+    using R = dd;
+    using V = float4;
+    static constexpr int NCHUNK = 6;
+    template <bool STREAM = true> TM_HD static void load(const V *blk, unsigned vh, unsigned i, Link<R> &u)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            V v = ld_link<STREAM>(blk + size_t(k) * vh + i);
+            u[k / 3][k % 3] = {dd{v.x, v.y}, dd{v.z, v.w}};
+        }
+        reconstruct_row2(u);
+    }
+    TM_HD static void store(V *blk, unsigned vh, unsigned i, const double *m)
+    {
+        for (int k = 0; k < 6; ++k) {
+            dd re = dd_from_double(m[2 * k]), im = dd_from_double(m[2 * k + 1]);
+            blk[size_t(k) * vh + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+};
+
 // ---------------------------------------------------------------- spin algebra
 // h = u + s A_mu l  (the upper pair of (1 + s gamma_mu) psi), s = +1 or -1.
 template <int MU, int S, typename R> TM_HD void project(const Spinor<R> &p, Half<R> &h)
@@ -450,18 +540,20 @@ template <bool DAG, typename R> TM_HD void link_mul(const Link<R> &u, const Half
 // the neighbour's index from the packed gauge field; StagedLinks reads both
 // from a tile [8 directions][NCHUNK][ts sites] that the block has copied to
 // shared memory (forward mu at 0..3, backward at 4..7).
-template <int P, int RECON> struct GlobalLinks {
+// STREAM: evict-first loads (each link is used once); otherwise default
+// caching, for launches in which several CTAs read the same links.
+template <int P, int RECON, bool STREAM = true> struct GlobalLinks {
     using L = LinkIO<P, RECON>;
     const typename L::V *links;
     unsigned vh, i;
     int p;
     template <int MU> TM_HD void fwd(const Nbrs &, Link<typename SpinorIO<P>::R> &u) const
     {
-        L::load(links + size_t(4 * p + MU) * L::NCHUNK * vh, vh, i, u);
+        L::template load<STREAM>(links + size_t(4 * p + MU) * L::NCHUNK * vh, vh, i, u);
     }
     template <int MU> TM_HD void bwd(const Nbrs &n, Link<typename SpinorIO<P>::R> &u) const
     {
-        L::load(links + size_t(4 * (1 - p) + MU) * L::NCHUNK * vh, vh, n.bwd[MU], u);
+        L::template load<STREAM>(links + size_t(4 * (1 - p) + MU) * L::NCHUNK * vh, vh, n.bwd[MU], u);
     }
 };
 
@@ -544,23 +636,29 @@ TM_HD void hop_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, R
 struct Coef {
     double d[8];  // au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im
     float f[8];   // the same, rounded once on the host for single-precision kernels
+    float xh[8], xl[8];  // and as double-float pairs
     Coef() = default;
     __host__ __device__ Coef(double au_re, double au_im, double al_re, double al_im, double bu_re, double bu_im,
                              double bl_re, double bl_im)
-        : d{au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im},
-          f{float(au_re), float(au_im), float(al_re), float(al_im), float(bu_re), float(bu_im), float(bl_re),
-            float(bl_im)}
+        : d{au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im}
     {
+        for (int k = 0; k < 8; ++k) {
+            f[k] = float(d[k]);
+            dd x = dd_from_double(d[k]);
+            xh[k] = x.hi;
+            xl[k] = x.lo;
+        }
     }
-    TM_HD const double *vals(double) const { return d; }
-    TM_HD const float *vals(float) const { return f; }
+    TM_HD double get(int k, double) const { return d[k]; }
+    TM_HD float get(int k, float) const { return f[k]; }
+    TM_HD dd get(int k, dd) const { return dd{xh[k], xl[k]}; }
 };
 
 template <typename R> TM_HD void epilogue(const Coef &k, const Spinor<R> &hop, const Spinor<R> *x, Spinor<R> &out)
 {
-    const R *v = k.vals(R(0));
-    cpx<R> au = {v[0], v[1]}, al = {v[2], v[3]};
-    cpx<R> bu = {v[4], v[5]}, bl = {v[6], v[7]};
+    const R z = R(0);
+    cpx<R> au = {k.get(0, z), k.get(1, z)}, al = {k.get(2, z), k.get(3, z)};
+    cpx<R> bu = {k.get(4, z), k.get(5, z)}, bl = {k.get(6, z), k.get(7, z)};
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll

@@ -83,6 +83,8 @@ extern "C" tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, con
         case F32 * 100 + 18: e = force_launch<F32, 18>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
         case F32 * 100 + 12: e = force_launch<F32, 12>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
         case F16 * 100 + 12: e = force_launch<F16, 12>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
+        case F64X * 100 + 18: e = force_launch<F64X, 18>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
+        case F64X * 100 + 12: e = force_launch<F64X, 12>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
         default: e = cudaErrorInvalidValue;
         }
     }

@@ -145,7 +145,7 @@ TM_HD void force_site(const Geom &g, int p, unsigned i, const typename LinkIO<P,
     Link<R> u;
     L::load(links + size_t(4 * p + MU) * L::NCHUNK * g.vh, g.vh, i, u);
     Mat<R> m;
-    force_link<MU>(u, Rx, Lx, Rxp, Lxp, R(kappa2), sgn, mode, m);
+    force_link<MU>(u, Rx, Lx, Rxp, Lxp, to_R<R>(kappa2), sgn, mode, m);
     double *o = F + (size_t(MU) * 2 * g.vh + lex_of(g, p, i)) * 18;
 #pragma unroll
     for (int a = 0; a < 3; ++a)

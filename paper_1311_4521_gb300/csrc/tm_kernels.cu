@@ -87,13 +87,15 @@ cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_par
     if (prec == F32 && recon == 18) return hop_dispatch<F32, 18>(g, dag, out_parity, links, in, out, x, k, s, block);
     if (prec == F32 && recon == 12) return hop_dispatch<F32, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
     if (prec == F16 && recon == 12) return hop_dispatch<F16, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
+    if (prec == F64X && recon == 18) return hop_dispatch<F64X, 18>(g, dag, out_parity, links, in, out, x, k, s, block);
+    if (prec == F64X && recon == 12) return hop_dispatch<F64X, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
     return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------ layouts
 int link_nchunk(int prec, int recon)
 {
-    if (prec == F64) return recon == 18 ? 9 : 6;
+    if (prec == F64 || prec == F64X) return recon == 18 ? 9 : 6;
     if (prec == F32) return recon == 18 ? 9 : 3;
     if (prec == F16 && recon == 12) return 3;
     return 0;
@@ -101,7 +103,7 @@ int link_nchunk(int prec, int recon)
 
 size_t link_chunk_bytes(int prec, int recon)
 {
-    if (prec == F64) return 16;
+    if (prec == F64 || prec == F64X) return 16;
     if (prec == F32) return recon == 18 ? 8 : 16;
     if (prec == F16) return 8;
     return 0;
@@ -141,6 +143,8 @@ cudaError_t launch_pack_gauge(const Geom &g, int prec, int recon, const double *
     TM_PACK(F32, 18)
     TM_PACK(F32, 12)
     TM_PACK(F16, 12)
+    TM_PACK(F64X, 18)
+    TM_PACK(F64X, 12)
 #undef TM_PACK
     return cudaErrorInvalidValue;
 }
@@ -152,7 +156,7 @@ __global__ void k_pack_spinor(unsigned vh, const double *__restrict__ in, void *
     unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= vh) return;
     Spinor<R> s;
-    for (int c = 0; c < 12; ++c) s[c / 3][c % 3] = {R(in[size_t(i) * 24 + 2 * c]), R(in[size_t(i) * 24 + 2 * c + 1])};
+    for (int c = 0; c < 12; ++c) s[c / 3][c % 3] = {to_R<R>(in[size_t(i) * 24 + 2 * c]), to_R<R>(in[size_t(i) * 24 + 2 * c + 1])};
     SpinorIO<P>::store(out, vh, i, s);
 }
 
@@ -175,6 +179,7 @@ cudaError_t launch_pack_spinor(unsigned vh, int prec, const double *in, void *ou
     if (vh == 0) return cudaSuccess;
     unsigned grid = (vh + 127) / 128;
     if (prec == F64) k_pack_spinor<F64><<<grid, 128, 0, s>>>(vh, in, out);
+    else if (prec == F64X) k_pack_spinor<F64X><<<grid, 128, 0, s>>>(vh, in, out);
     else if (prec == F32) k_pack_spinor<F32><<<grid, 128, 0, s>>>(vh, in, out);
     else if (prec == F16) k_pack_spinor<F16><<<grid, 128, 0, s>>>(vh, in, out);
     else return cudaErrorInvalidValue;
@@ -186,6 +191,7 @@ cudaError_t launch_unpack_spinor(unsigned vh, int prec, const void *in, double *
     if (vh == 0) return cudaSuccess;
     unsigned grid = (vh + 127) / 128;
     if (prec == F64) k_unpack_spinor<F64><<<grid, 128, 0, s>>>(vh, in, out);
+    else if (prec == F64X) k_unpack_spinor<F64X><<<grid, 128, 0, s>>>(vh, in, out);
     else if (prec == F32) k_unpack_spinor<F32><<<grid, 128, 0, s>>>(vh, in, out);
     else if (prec == F16) k_unpack_spinor<F16><<<grid, 128, 0, s>>>(vh, in, out);
     else return cudaErrorInvalidValue;

@@ -20,10 +20,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtmhop.so")
 
 TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE, TM_ERR_TIMEOUT, TM_ERR_UNSUPPORTED = range(7)
-TM_F64, TM_F32, TM_F16 = 0, 1, 2
+TM_F64, TM_F32, TM_F16, TM_F64X = 0, 1, 2, 3
 TM_EO, TM_OE = 0, 1
 TM_FORCE_SU3, TM_FORCE_GRAD = 0, 1
-PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16}
+PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16, "f64x": TM_F64X}
 
 
 class CgParams(ctypes.Structure):

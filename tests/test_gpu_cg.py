@@ -147,3 +147,21 @@ def test_cg_production_size_oracle_residual(ctx):
         xs = ctx.unpack(x, vh, "f64").cpu().numpy()
         assert oracle_relres(dims, U, xs, b, 0.1394, 0.0015) <= 1.05e-10
     gh.close()
+
+
+@pytest.mark.parametrize("inner", ["f64x", "f32", "f16"])
+def test_cg_double_float_outer_solver(ctx, inner):
+    """U_hi in double-float storage (TM_F64X): x and b packed as F64X; plain
+    F64X CG or mixed precision with F64X reliable updates."""
+    from paper_1311_4521_gb300 import tmhop
+    dims = (6, 4, 8, 10)
+    U = F.gauge_field(dims, F.SEED_CG_48, "near", 0.3)
+    vh = int(np.prod(dims)) // 2
+    b = F.gaussian_spinor(vh, F.SEED_CG_48, 1)
+    gh = ctx.gauge(dims, U, "f64x", 18)
+    gl = None if inner == "f64x" else ctx.gauge(dims, U, inner, 12)
+    x = ctx.empty(vh, "f64x").zero_()
+    st, info = ctx.cg(gh, x, ctx.pack(b, "f64x"), 0.1394, 0.0015, 1e-10, 30000, gl)
+    assert st == tmhop.TM_OK, info
+    xs = ctx.unpack(x, vh, "f64x").cpu().numpy()
+    assert oracle_relres(dims, U, xs, b, 0.1394, 0.0015) <= 1.05e-10

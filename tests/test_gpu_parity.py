@@ -13,8 +13,8 @@ from paper_1311_4521_gb300 import fields as F
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 5e-3}
-STORAGE = [("f64", 18), ("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12)]
+TOL = {"f64": 1e-13, "f64x": 1e-13, "f32": 1e-6, "f16": 5e-3}
+STORAGE = [("f64", 18), ("f64", 12), ("f64x", 18), ("f64x", 12), ("f32", 18), ("f32", 12), ("f16", 12)]
 
 
 @pytest.fixture(scope="module")
@@ -75,7 +75,7 @@ def test_Qtm_small(ctx, small, prec, recon, sign):
 # periodic and antiperiodic boundaries in several directions
 @pytest.mark.parametrize("dims,bc", [((2, 2, 2, 2), (-1, 1, 1, 1)), ((6, 4, 2, 10), (-1, 1, 1, 1)),
                                      ((10, 6, 4, 2), (1, -1, 1, -1)), ((4, 14, 6, 6), (-1, -1, -1, -1))])
-@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 12), ("f16", 12)])
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64x", 18), ("f32", 12), ("f16", 12)])
 def test_ragged_lattices(ctx, dims, bc, prec, recon):
     vh = int(np.prod(dims)) // 2
     U = F.gauge_field(dims, 7, "random")
@@ -88,11 +88,11 @@ def test_ragged_lattices(ctx, dims, bc, prec, recon):
     assert rel(got, want) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f64x", "f32", "f16"])
 def test_pack_roundtrip(ctx, prec):
     psi = F.gaussian_spinor(1000, 3, 3)
     back = ctx.unpack(ctx.pack(psi, prec), 1000, prec).cpu().numpy()
-    assert rel(back, psi) < {"f64": 0, "f32": 1e-7, "f16": 1e-3}[prec] + 1e-300
+    assert rel(back, psi) < {"f64": 0, "f64x": 1e-14, "f32": 1e-7, "f16": 1e-3}[prec] + 1e-300
     # an all-zero site survives the half-precision norm
     z = np.zeros((3, 4, 3), complex)
     assert np.all(ctx.unpack(ctx.pack(z, prec), 3, prec).cpu().numpy() == 0)
@@ -139,7 +139,7 @@ def prod():
     return dims, U, psi, want
 
 
-@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 12), ("f16", 12)])
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64x", 18), ("f32", 12), ("f16", 12)])
 def test_Qtm_production_size(ctx, prod, prec, recon):
     dims, U, psi, want = prod
     got = gpu_apply(ctx, dims, U, psi, prec, recon, "qtm", kappa=0.1394, mu=0.0015)
