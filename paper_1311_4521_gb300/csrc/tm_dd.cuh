@@ -96,6 +96,25 @@ TM_HD dd &operator-=(dd &a, dd b) { return a = a - b; }
 
 TM_HD dd abs_dd(dd x) { return x.hi < 0.f ? -x : x; }
 
+// Compensated dot-product accumulator (Ogita, Rump and Oishi, "Accurate sum
+// and dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2, extended to
+// double-float factors): the exact product of the high parts goes through
+// TwoSum into s, every error term and the cross products of high and low
+// parts are summed in FP32 into c; the result is as if computed with twice
+// the working precision and normalised once at the end.
+struct dot2 {
+    float s = 0.f, c = 0.f;
+    TM_HD void add(dd x, dd y)  // += x y
+    {
+        dd p = two_prod(x.hi, y.hi);
+        dd t = two_sum(s, p.hi);
+        s = t.hi;
+        c = f_add(c, f_add(t.lo, f_fma(x.hi, y.lo, f_fma(x.lo, y.hi, p.lo))));
+    }
+    TM_HD void sub(dd x, dd y) { add(dd{-x.hi, -x.lo}, y); }  // -= x y
+    TM_HD dd result() const { return two_sum(s, c); }
+};
+
 // nearest double-float to a double: hi = fl32(x), lo = fl32(x - hi)
 TM_HD dd dd_from_double(double x)
 {

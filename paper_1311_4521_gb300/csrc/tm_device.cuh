@@ -498,6 +498,14 @@ template <int MU, int S, typename R> TM_HD void project(const Spinor<R> &p, Half
 // (1 except for half-precision storage); it rides on fused multiply-adds.
 template <typename R> TM_HD cpx<R> fmadd(R w, cpx<R> a, cpx<R> acc) { return {acc.re + w * a.re, acc.im + w * a.im}; }
 
+// Double-float storage has no site scale, so w is +1 or -1: a sign flip and
+// an addition instead of a double-float product.
+TM_HD cpx<dd> fmadd(dd w, cpx<dd> a, cpx<dd> acc)
+{
+    const float s = w.hi;
+    return {acc.re + dd{s * a.re.hi, s * a.re.lo}, acc.im + dd{s * a.im.hi, s * a.im.lo}};
+}
+
 template <int MU, int S, typename R> TM_HD void accumulate(const Half<R> &h, R w, Spinor<R> &a)
 {
     const R ws = S > 0 ? w : -w;
@@ -532,6 +540,36 @@ template <bool DAG, typename R> TM_HD void link_mul(const Link<R> &u, const Half
 #pragma unroll
             for (int b = 0; b < 3; ++b) acc = DAG ? cjmadd(u[b][a], h[s][b], acc) : cmadd(u[a][b], h[s][b], acc);
             r[s][a] = acc;
+        }
+}
+
+// Double-float link multiply: each output component is a dot product of six
+// real terms, summed with the compensated accumulator instead of six
+// double-float multiply-adds.
+template <bool DAG> TM_HD void link_mul(const Link<dd> &u, const Half<dd> &h, Half<dd> &r)
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            dot2 re, im;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const cpx<dd> w = DAG ? u[b][a] : u[a][b];
+                const cpx<dd> x = h[s][b];
+                if (DAG) {  // conj(w) x
+                    re.add(w.re, x.re);
+                    re.add(w.im, x.im);
+                    im.add(w.re, x.im);
+                    im.sub(w.im, x.re);
+                } else {  // w x
+                    re.add(w.re, x.re);
+                    re.sub(w.im, x.im);
+                    im.add(w.re, x.im);
+                    im.add(w.im, x.re);
+                }
+            }
+            r[s][a] = {re.result(), im.result()};
         }
 }
 
