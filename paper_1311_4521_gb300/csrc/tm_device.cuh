@@ -39,7 +39,10 @@
 #ifndef TM_HOP_MINB_F16
 #define TM_HOP_MINB_F16 5
 #endif
-#define TM_HOP_MINB(P) ((P) == 0 || (P) == 3 ? 2 : (P) == 1 ? TM_HOP_MINB_F32 : TM_HOP_MINB_F16)
+#ifndef TM_HOP_MINB_F64X
+#define TM_HOP_MINB_F64X 3
+#endif
+#define TM_HOP_MINB(P) ((P) == 0 ? 2 : (P) == 3 ? TM_HOP_MINB_F64X : (P) == 1 ? TM_HOP_MINB_F32 : TM_HOP_MINB_F16)
 
 namespace twm {
 
@@ -643,6 +646,65 @@ TM_HD void hop_dir(const Geom &g, const Nbrs &n, const Src &src, const void *in,
     }
 }
 
+// The 8 hops as a loop that is not unrolled, for double-float storage: its
+// arithmetic expands to so many FP32 instructions that the fully unrolled
+// stencil overflows the instruction cache (ncu: warps stalled on
+// "no instruction").  Each link multiply is instantiated once; the
+// direction-dependent spin algebra is selected by small switches, and all
+// register arrays keep static indices.
+template <int P, bool DAG, class Src>
+TM_HD void hop_site_rolled(const Geom &g, const Nbrs &n, const Src &src, const void *in,
+                           Spinor<typename SpinorIO<P>::R> &acc)
+{
+    using R = typename SpinorIO<P>::R;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const int mu = k >> 1;
+        const bool fwd = (k & 1) == 0;
+        unsigned j;
+        bool wrap;
+        switch (k) {
+        case 0: j = n.fwd[0]; wrap = n.wf[0]; break;
+        case 1: j = n.bwd[0]; wrap = n.wb[0]; break;
+        case 2: j = n.fwd[1]; wrap = n.wf[1]; break;
+        case 3: j = n.bwd[1]; wrap = n.wb[1]; break;
+        case 4: j = n.fwd[2]; wrap = n.wf[2]; break;
+        case 5: j = n.bwd[2]; wrap = n.wb[2]; break;
+        case 6: j = n.fwd[3]; wrap = n.wf[3]; break;
+        default: j = n.bwd[3]; wrap = n.wb[3]; break;
+        }
+        Spinor<R> s;
+        Half<R> h, r;
+        Link<R> u;
+        R w = SpinorIO<P>::load_raw(in, g.vh, j, s);
+        if (wrap && g.anti[mu]) w = -w;
+        switch (k) {
+        case 0: project<0, SF>(s, h); src.template fwd<0>(n, u); break;
+        case 1: project<0, SB>(s, h); src.template bwd<0>(n, u); break;
+        case 2: project<1, SF>(s, h); src.template fwd<1>(n, u); break;
+        case 3: project<1, SB>(s, h); src.template bwd<1>(n, u); break;
+        case 4: project<2, SF>(s, h); src.template fwd<2>(n, u); break;
+        case 5: project<2, SB>(s, h); src.template bwd<2>(n, u); break;
+        case 6: project<3, SF>(s, h); src.template fwd<3>(n, u); break;
+        default: project<3, SB>(s, h); src.template bwd<3>(n, u); break;
+        }
+        if (fwd) link_mul<false>(u, h, r);
+        else link_mul<true>(u, h, r);
+        switch (k) {
+        case 0: accumulate<0, SF>(r, w, acc); break;
+        case 1: accumulate<0, SB>(r, w, acc); break;
+        case 2: accumulate<1, SF>(r, w, acc); break;
+        case 3: accumulate<1, SB>(r, w, acc); break;
+        case 4: accumulate<2, SF>(r, w, acc); break;
+        case 5: accumulate<2, SB>(r, w, acc); break;
+        case 6: accumulate<3, SF>(r, w, acc); break;
+        default: accumulate<3, SB>(r, w, acc); break;
+        }
+    }
+}
+
 template <int P, bool DAG, class Src>
 TM_HD void hop_site_src(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<typename SpinorIO<P>::R> &acc)
 {
@@ -651,10 +713,14 @@ TM_HD void hop_site_src(const Geom &g, const Nbrs &n, const Src &src, const void
     for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[s][c] = {R(0), R(0)};
-    hop_dir<P, DAG, 0>(g, n, src, in, acc);
-    hop_dir<P, DAG, 1>(g, n, src, in, acc);
-    hop_dir<P, DAG, 2>(g, n, src, in, acc);
-    hop_dir<P, DAG, 3>(g, n, src, in, acc);
+    if constexpr (P == F64X) {
+        hop_site_rolled<P, DAG>(g, n, src, in, acc);
+    } else {
+        hop_dir<P, DAG, 0>(g, n, src, in, acc);
+        hop_dir<P, DAG, 1>(g, n, src, in, acc);
+        hop_dir<P, DAG, 2>(g, n, src, in, acc);
+        hop_dir<P, DAG, 3>(g, n, src, in, acc);
+    }
 }
 
 // The hop at output site i of parity p with links read from the packed gauge field.
