@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Hopping-matrix GB/s & Gflop/s vs HBM roofline; mixed vs FP64 CG time to 1e-10"
 DIMS = (32, 32, 32, 64)
 KAPPA, MU = 0.1394, 0.0015
+HBM_NOMINAL_GBS = 7900.0     # nominal HBM3e bandwidth of a GB300, for context beside the measured copy peak
 SAMPLE_DIMS = (16, 16, 16, 16)       # bounded sample for the CPU reference arm
 L2_BYTES = 129 * 2 ** 20
 REAL = {"f64": 8, "f64x": 8, "f32": 4, "f16": 2}
@@ -352,14 +353,16 @@ def gpu_arm(args) -> None:
                 "ms_per_qtm": round(step_ms, 4), "GBps": round(vh * abp["qtm"] / (step_ms * 1e-3) / 1e9, 1),
                 "gflops": round(vh * QTM_FLOPS / (step_ms * 1e-3) / 1e9, 1),
                 "kernel_b_ms": round(b_ms, 4), "kernel_b_GBps": round(bgbs, 1),
-                "kernel_b_hbm_frac": round(bgbs / hbm_peak, 4), "kernel_a_ms": round(a_ms, 4)}
+                "kernel_b_hbm_frac": round(bgbs / hbm_peak, 4),
+                "kernel_b_nominal_frac": round(bgbs / HBM_NOMINAL_GBS, 4), "kernel_a_ms": round(a_ms, 4)}
             gp.close()
             del sp, dp
 
     # ---- CG on Q^dag Q to true relative residual 1e-10: FP64 vs mixed precision
     cg = None
+    cg_host = None
     if not args.no_cg:
-        cg = cg_section(args, ctx, tmhop, torch, F, allmax, barrier)
+        cg, cg_host = cg_section(args, ctx, tmhop, torch, F, allmax, barrier, keep_host=(rank == 0 and not args.no_cpu))
 
     # ---- batching: 12 right-hand sides on 32^3x64 and 8 uneven lattices, FP32 storage
     batch = None
@@ -388,6 +391,24 @@ def gpu_arm(args) -> None:
         cpu = {"value": round(vh * ab["qtm"] / dt / 1e9, 3), "unit": "GB/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
                "kind": "oracle", "sample": f"{n} full Q_tm applications on {lat} (FP64, OpenMP over sites)",
                "s_per_qtm": round(dt, 3), "gflops": round(vh * QTM_FLOPS / dt / 1e9, 3)}
+        if cg_host is not None:
+            # the FP64 oracle CG on the CG lattice would take minutes: time one
+            # call with a single iteration (three Q^dag Q applications: the
+            # initial residual, the iteration, the final true residual) and
+            # scale by the GPU FP64 solver's iteration count
+            cdims, cU, cb = cg_host
+            t = time.perf_counter()
+            O.cg_QdagQ(cdims, cU, cb, KAPPA, MU, tol=1e-10, maxiter=1)
+            per_it = (time.perf_counter() - t) / 3
+            iters = cg["fp64"]["iters"]
+            cpu["cg_estimate"] = {
+                "lattice": list(cdims), "kind": "estimate", "s_per_iter": round(per_it, 3), "iters": iters,
+                "seconds": round(per_it * iters, 1),
+                "speedup_of_gpu_fp64": round(per_it * iters / cg["fp64"]["seconds"], 1),
+                "speedup_of_gpu_best": round(per_it * iters / min(v["seconds"] for v in cg.values()
+                                                                   if isinstance(v, dict) and "seconds" in v), 1),
+                "how": "one oracle CG call with maxiter=1 (3 Q^dag Q applications) / 3 x the GPU FP64 iteration count"}
+            del cg_host, cU, cb
 
     if rank == 0:
         line = {
@@ -411,12 +432,14 @@ def gpu_arm(args) -> None:
         dist.destroy_process_group()
 
 
-def cg_section(args, ctx, tmhop, torch, F, allmax, barrier) -> dict:
+def cg_section(args, ctx, tmhop, torch, F, allmax, barrier, keep_host=False):
     """Time to a true relative residual of 1e-10 for Q^dag Q x = b on the CG
     lattice (48^3x96 by default, U = exp(0.3 i A), Gaussian source): plain
     FP64 CG against mixed precision with FP32 and FP16 storage (FP32
     arithmetic, FP64 reliable updates).  Each solver runs once to warm up,
-    then once timed with CUDA events around the (synchronous) call."""
+    then once timed with CUDA events around the (synchronous) call.
+    Returns the results and, with keep_host, the host links and source (for
+    the oracle's time estimate), else None."""
     dims = args.cg_lattice
     vh = int(np.prod(dims)) // 2
     U = F.gauge_field(dims, F.SEED_CG_48, "near", 0.3)
@@ -424,6 +447,7 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier) -> dict:
     gh = ctx.gauge(dims, U, "f64", 18)
     gx = ctx.gauge(dims, U, "f64x", 18)
     lo = {"mixed_f32": ctx.gauge(dims, U, "f32", 12), "mixed_f16": ctx.gauge(dims, U, "f16", 12)}
+    host = (dims, U, b) if keep_host else None
     del U
     bd = ctx.pack(b, "f64")
     bx = ctx.pack(b, "f64x")
@@ -453,14 +477,15 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier) -> dict:
                          "~48-bit significand); convergence still judged on the true residual")
     for g in [gh, gx] + list(lo.values()):
         g.close()
-    return out
+    return out, host
 
 
 def only_section(args, ctx, tmhop, torch, F, U, psi, dims, vh, barrier, allmax) -> dict:
     """One part of the benchmark alone, for profiling captures:
     batch-qtm  Q_tm on 12 right-hand sides of --lattice, --steps batched calls;
     cg         the CG section on --cg-lattice;
-    force      the force kernel on --lattice, --steps calls;
+    force      the force call (3 hops + assembly by --force-scheme) on
+               --lattice, --steps calls;
     solve      the even-odd full-lattice solve on --lattice (FP32 inner)."""
     res = {"only": args.only, "lattice": list(dims)}
     stream = torch.cuda.current_stream()
@@ -481,17 +506,20 @@ def only_section(args, ctx, tmhop, torch, F, U, psi, dims, vh, barrier, allmax) 
         g.close()
     elif args.only == "cg":
         args.cg_lattice = dims
-        res.update(cg_section(args, ctx, tmhop, torch, F, allmax, barrier))
+        res.update(cg_section(args, ctx, tmhop, torch, F, allmax, barrier)[0])
     elif args.only == "force":
         g = ctx.gauge(dims, U, args.prec, args.recon)
         xp = ctx.pack(psi, args.prec)
+        sch = {"owner": tmhop.TM_FORCE_OWNER, "atomic": tmhop.TM_FORCE_ATOMIC,
+               "halo": tmhop.TM_FORCE_HALO}[args.force_scheme]
+        res["scheme"] = args.force_scheme
         for _ in range(args.warmup):
-            ctx.force(g, xp, KAPPA, MU)
+            ctx.force(g, xp, KAPPA, MU, tmhop.TM_FORCE_SU3, sch)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            ctx.force(g, xp, KAPPA, MU)
+            ctx.force(g, xp, KAPPA, MU, tmhop.TM_FORCE_SU3, sch)
         e1.record(stream)
         torch.cuda.synchronize()
         res["ms_per_force"] = e0.elapsed_time(e1) / args.steps
@@ -509,9 +537,12 @@ def only_section(args, ctx, tmhop, torch, F, U, psi, dims, vh, barrier, allmax) 
 
 def grad_section(args, ctx, tmhop, torch, F) -> dict:
     """24^3x48, U = exp(0.3 i A): the action S = phi^dag (Q^dag Q)^-1 phi
-    through autograd (forward solve + backward force), and the force
-    kernel alone, FP64 and FP32 storage (for information: correctness is
-    covered by the tests)."""
+    through autograd (forward solve + backward force), and the force call
+    alone (its three hops plus the force assembly) for each way of
+    assembling the per-link force (one owner thread per link, pushes with
+    FP64 atomics, pushes into private buffers plus a summing pass), FP64
+    and FP32 storage (for information: correctness is covered by the
+    tests)."""
     from paper_1311_4521_gb300 import autograd
     dims = (24, 24, 24, 48)
     vh = int(np.prod(dims)) // 2
@@ -534,17 +565,21 @@ def grad_section(args, ctx, tmhop, torch, F) -> dict:
             torch.cuda.synchronize()
         g = ctx.gauge(dims, U, fprec, 18 if fprec == "f64" else 12)
         xp = ctx.pack(gphi.detach() / 2, fprec)
-        fe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ctx.force(g, xp, KAPPA, MU)
-        fe[0].record(stream)
-        for _ in range(10):
-            ctx.force(g, xp, KAPPA, MU)
-        fe[1].record(stream)
-        torch.cuda.synchronize()
+        sch_ms = {}
+        for name, sch in (("owner", tmhop.TM_FORCE_OWNER), ("atomic", tmhop.TM_FORCE_ATOMIC),
+                          ("halo", tmhop.TM_FORCE_HALO)):
+            fe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ctx.force(g, xp, KAPPA, MU, tmhop.TM_FORCE_SU3, sch)
+            fe[0].record(stream)
+            for _ in range(10):
+                ctx.force(g, xp, KAPPA, MU, tmhop.TM_FORCE_SU3, sch)
+            fe[1].record(stream)
+            torch.cuda.synchronize()
+            sch_ms[name] = round(fe[0].elapsed_time(fe[1]) / 10, 4)
         g.close()
         out[f"{inner}_solve_{fprec}_force"] = {
             "forward_s": round(e0.elapsed_time(e1) / 1e3, 4), "backward_s": round(e1.elapsed_time(e2) / 1e3, 4),
-            "force_ms": round(fe[0].elapsed_time(fe[1]) / 10, 4), "S": float(S.item())}
+            "force_ms": sch_ms["owner"], "force_ms_by_scheme": sch_ms, "S": float(S.item())}
     return out
 
 
@@ -716,6 +751,8 @@ def main() -> None:
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--only", choices=["batch-qtm", "cg", "force", "solve"], default=None,
                     help="run one section alone (for profiling captures)")
+    ap.add_argument("--force-scheme", choices=["owner", "atomic", "halo"], default="owner",
+                    help="force assembly for --only force")
     ap.add_argument("--cg-lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=(48, 48, 48, 96))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -219,6 +219,25 @@ enum { TM_FORCE_SU3 = 0,    /* F in su(3): U -> exp(eps T) U changes S by eps <T
 tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa, double mu,
                    int mode, void *stream);
 
+/* How tm_force_ex assembles the per-link force.  Every link's force has two
+ * parts, one from each hop that uses the link; the paper (Sec. 2.4) weighs
+ * updating a shared derivative field with "atomic" directives against
+ * per-site "halo memory" with a second accumulation loop.
+ *   TM_FORCE_OWNER  one thread per link computes both parts (tm_force)
+ *   TM_FORCE_ATOMIC one thread per site pushes the forward part of its 4
+ *                   links and the backward part of the 4 links ending there
+ *                   with FP64 atomic adds into F (zeroed first); with two
+ *                   addends per entry the result does not depend on order
+ *   TM_FORCE_HALO   the same pushes into two private buffers, then a second
+ *                   pass F = forward + backward (no atomics, more traffic) */
+enum { TM_FORCE_OWNER = 0, TM_FORCE_ATOMIC = 1, TM_FORCE_HALO = 2 };
+
+/* tm_force with a choice of scheme (the push schemes for TM_F64 and TM_F32
+ * handles only; TM_ERR_UNSUPPORTED otherwise).  Same result up to rounding;
+ * TM_FORCE_ATOMIC and TM_FORCE_HALO agree bit for bit. */
+tm_status tm_force_ex(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa, double mu,
+                      int mode, int scheme, void *stream);
+
 /* ---- batches ------------------------------------------------------------ */
 
 /* Q_tm(sign*mu) applied to nsys even fields (out_e[k] = Q in_e[k] with gauge

@@ -1,8 +1,10 @@
 // tm_force.cu -- the fermion force of S = phi^dag (Q^dag Q)^-1 phi and the
-// complex gradient dS/dU, one thread per link, no atomics: every link is
-// written by exactly one thread, so the race the paper discusses for the
-// HMC derivative (Sec. 2.4: atomic updates of the derivative field) cannot
-// occur.
+// complex gradient dS/dU.  Default assembly: one thread per link, no
+// atomics: every link is written by exactly one thread, so the race the
+// paper discusses for the HMC derivative (Sec. 2.4: atomic updates of the
+// derivative field) cannot occur.  The two push schemes of that discussion
+// (atomic adds, and private buffers summed in a second pass) are built
+// beside it for comparison.
 #include <string>
 
 #include "tm_force.cuh"
@@ -15,9 +17,12 @@ __global__ void __launch_bounds__(128) k_force(Geom g, const typename LinkIO<P, 
                                                const void *Xe, const void *Ye, const void *Zo, const void *Bo,
                                                double kappa2, int mode, double *F)
 {
-    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    // the 8 (parity, direction) slices of one tile of sites are consecutive
+    // blocks, so the spinors that neighbouring slices share come from L2
+    const int slice = blockIdx.x & 7;
+    const unsigned i = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
     if (i >= g.vh) return;
-    const int p = blockIdx.y >> 2, mu = blockIdx.y & 3;   // uniform per block
+    const int p = slice >> 2, mu = slice & 3;   // uniform per block
     switch (mu) {
     case 0: force_site<P, RECON, 0>(g, p, i, links, Xe, Ye, Zo, Bo, kappa2, mode, F); break;
     case 1: force_site<P, RECON, 1>(g, p, i, links, Xe, Ye, Zo, Bo, kappa2, mode, F); break;
@@ -30,9 +35,103 @@ template <int P, int RECON>
 static cudaError_t force_launch(const tm_gauge *U, const void *Xe, const void *Ye, const void *Zo, const void *Bo,
                                 double kappa2, int mode, double *F, cudaStream_t s)
 {
-    dim3 grid((U->geom.vh + 127) / 128, 8);
+    const unsigned grid = 8 * ((U->geom.vh + 127) / 128);
     k_force<P, RECON><<<grid, 128, 0, s>>>(U->geom, static_cast<const typename LinkIO<P, RECON>::V *>(U->links), Xe,
                                           Ye, Zo, Bo, kappa2, mode, F);
+    return cudaGetLastError();
+}
+
+// ---- push schemes (the comparison of Sec. 2.4: atomics vs "halo memory")
+// One thread per site y; for each direction it computes the forward part of
+// link (mu, y) and the backward part of link (mu, y - mu).  Every link thus
+// has two writers: its base and its tip.
+enum { PUSH_ATOMIC = 1, PUSH_HALO = 2 };
+
+template <int P, int RECON, int MU, int SCHEME>
+__device__ __forceinline__ void push_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, RECON>::V *links,
+                                          const void *Xe, const void *Ye, const void *Zo, const void *Bo,
+                                          double kappa2, int mode, double *F, double *Hf, double *Hb)
+{
+    using R = typename SpinorIO<P>::R;
+    using L = LinkIO<P, RECON>;
+    Nbrs n;
+    neighbours(g, p, i, n);
+    // fields at y: L(y) (own), R at the two neighbours
+    Spinor<R> Ly, Rf, Rb;
+    const void *Rnb = p == 0 ? Zo : Xe;  // R on the other parity
+    if (p == 0) {
+        SpinorIO<P>::load(Ye, g.vh, i, Ly);
+        apply_g5(Ly);
+    } else {
+        SpinorIO<P>::load(Bo, g.vh, i, Ly);
+    }
+    SpinorIO<P>::load(Rnb, g.vh, n.fwd[MU], Rf);
+    SpinorIO<P>::load(Rnb, g.vh, n.bwd[MU], Rb);
+    Link<R> uf, ub;
+    L::load(links + size_t(4 * p + MU) * L::NCHUNK * g.vh, g.vh, i, uf);
+    L::load(links + size_t(4 * (1 - p) + MU) * L::NCHUNK * g.vh, g.vh, n.bwd[MU], ub);
+    const R sf = (n.wf[MU] && g.anti[MU]) ? R(-1) : R(1);
+    const R sb = (n.wb[MU] && g.anti[MU]) ? R(-1) : R(1);
+    Mat<R> mf, mb;
+    force_part_fwd<MU>(uf, Rf, Ly, to_R<R>(kappa2), sf, mode, mf);
+    force_part_bwd<MU>(ub, Rb, Ly, to_R<R>(kappa2), sb, mode, mb);
+    const size_t V = 2 * size_t(g.vh);
+    const size_t lf = size_t(MU) * V + lex_of(g, p, i);              // link (mu, y)
+    const size_t lb = size_t(MU) * V + lex_of(g, 1 - p, n.bwd[MU]);  // link (mu, y - mu)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int k = 6 * a + 2 * b;
+            if (SCHEME == PUSH_ATOMIC) {
+                atomicAdd(F + lf * 18 + k, double(mf[a][b].re));
+                atomicAdd(F + lf * 18 + k + 1, double(mf[a][b].im));
+                atomicAdd(F + lb * 18 + k, double(mb[a][b].re));
+                atomicAdd(F + lb * 18 + k + 1, double(mb[a][b].im));
+            } else {
+                Hf[lf * 18 + k] = double(mf[a][b].re);
+                Hf[lf * 18 + k + 1] = double(mf[a][b].im);
+                Hb[lb * 18 + k] = double(mb[a][b].re);
+                Hb[lb * 18 + k + 1] = double(mb[a][b].im);
+            }
+        }
+}
+
+template <int P, int RECON, int SCHEME>
+__global__ void __launch_bounds__(128) k_force_push(Geom g, const typename LinkIO<P, RECON>::V *__restrict__ links,
+                                                    const void *Xe, const void *Ye, const void *Zo, const void *Bo,
+                                                    double kappa2, int mode, double *F, double *Hf, double *Hb)
+{
+    const int slice = blockIdx.x & 7;   // as in k_force
+    const unsigned i = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    const int p = slice >> 2, mu = slice & 3;
+    switch (mu) {
+    case 0: push_site<P, RECON, 0, SCHEME>(g, p, i, links, Xe, Ye, Zo, Bo, kappa2, mode, F, Hf, Hb); break;
+    case 1: push_site<P, RECON, 1, SCHEME>(g, p, i, links, Xe, Ye, Zo, Bo, kappa2, mode, F, Hf, Hb); break;
+    case 2: push_site<P, RECON, 2, SCHEME>(g, p, i, links, Xe, Ye, Zo, Bo, kappa2, mode, F, Hf, Hb); break;
+    default: push_site<P, RECON, 3, SCHEME>(g, p, i, links, Xe, Ye, Zo, Bo, kappa2, mode, F, Hf, Hb); break;
+    }
+}
+
+// Second pass of the halo-memory scheme: F = Hf + Hb, element by element.
+__global__ void __launch_bounds__(256) k_force_halo_sum(size_t n, const double *Hf, const double *Hb, double *F)
+{
+    const size_t k = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+    if (k < n) F[k] = Hf[k] + Hb[k];
+}
+
+template <int P, int RECON>
+static cudaError_t force_push_launch(const tm_gauge *U, const void *Xe, const void *Ye, const void *Zo, const void *Bo,
+                                     double kappa2, int mode, int scheme, double *F, double *Hf, double *Hb,
+                                     cudaStream_t s)
+{
+    const unsigned grid = 8 * ((U->geom.vh + 127) / 128);
+    const auto *l = static_cast<const typename LinkIO<P, RECON>::V *>(U->links);
+    if (scheme == PUSH_ATOMIC)
+        k_force_push<P, RECON, PUSH_ATOMIC><<<grid, 128, 0, s>>>(U->geom, l, Xe, Ye, Zo, Bo, kappa2, mode, F, Hf, Hb);
+    else
+        k_force_push<P, RECON, PUSH_HALO><<<grid, 128, 0, s>>>(U->geom, l, Xe, Ye, Zo, Bo, kappa2, mode, F, Hf, Hb);
     return cudaGetLastError();
 }
 
@@ -47,8 +146,8 @@ Coef coef_force_b(double mut)
 
 using namespace twm;
 
-extern "C" tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa,
-                              double mu, int mode, void *stream)
+extern "C" tm_status tm_force_ex(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa,
+                                 double mu, int mode, int scheme, void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
     if (!U || !F_dev || !X_e_dev) {
@@ -59,13 +158,25 @@ extern "C" tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, con
         ctx->err = "tm_force: mode must be TM_FORCE_SU3 or TM_FORCE_GRAD";
         return TM_ERR_ARG;
     }
+    if (scheme != TM_FORCE_OWNER && scheme != TM_FORCE_ATOMIC && scheme != TM_FORCE_HALO) {
+        ctx->err = "tm_force_ex: scheme must be TM_FORCE_OWNER, TM_FORCE_ATOMIC or TM_FORCE_HALO";
+        return TM_ERR_ARG;
+    }
+    if (scheme != TM_FORCE_OWNER && U->prec != TM_F64 && U->prec != TM_F32) {
+        ctx->err = "tm_force_ex: the push schemes are built for TM_F64 and TM_F32 handles";
+        return TM_ERR_UNSUPPORTED;
+    }
     const unsigned vh = U->geom.vh;
     const size_t fb = (spinor_bytes(vh, U->prec) + 255) & ~size_t(255);
+    const size_t nF = size_t(4) * 2 * vh * 18;   // doubles in one force field
+    const size_t hb = scheme == TM_FORCE_HALO ? (nF * sizeof(double) + 255) & ~size_t(255) : 0;
     void *base = nullptr;
-    tm_status st = tm_ctx_workspace(ctx, 3 * fb, &base);
+    tm_status st = tm_ctx_workspace(ctx, 3 * fb + 2 * hb, &base);
     if (st != TM_OK) return st;
     char *c = static_cast<char *>(base);
     void *Ye = c, *Zo = c + fb, *Bo = c + 2 * fb;
+    double *Hf = hb ? reinterpret_cast<double *>(c + 3 * fb) : nullptr;
+    double *Hb = hb ? reinterpret_cast<double *>(c + 3 * fb + hb) : nullptr;
     const double mut = 2.0 * kappa * mu;
     cudaStream_t s = (cudaStream_t)stream;
     // Z = M_oo^-1 H_oe X, Y = Q X, B = gamma5 (M_oo^-1)^dag H_oe Y
@@ -75,8 +186,8 @@ extern "C" tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, con
         e = launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, Zo, Ye, X_e_dev, coef_qtm_b(kappa, mut), s, 128);
     if (e == cudaSuccess)
         e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, Ye, Bo, nullptr, coef_force_b(mut), s, 128);
-    if (e == cudaSuccess) {
-        const double k2 = kappa * kappa;
+    const double k2 = kappa * kappa;
+    if (e == cudaSuccess && scheme == TM_FORCE_OWNER) {
         switch (U->prec * 100 + U->recon) {
         case F64 * 100 + 18: e = force_launch<F64, 18>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
         case F64 * 100 + 12: e = force_launch<F64, 12>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
@@ -87,10 +198,32 @@ extern "C" tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, con
         case F64X * 100 + 12: e = force_launch<F64X, 12>(U, X_e_dev, Ye, Zo, Bo, k2, mode, F_dev, s); break;
         default: e = cudaErrorInvalidValue;
         }
+    } else if (e == cudaSuccess) {
+        const int sch = scheme == TM_FORCE_ATOMIC ? PUSH_ATOMIC : PUSH_HALO;
+        if (scheme == TM_FORCE_ATOMIC) e = cudaMemsetAsync(F_dev, 0, nF * sizeof(double), s);
+        if (e == cudaSuccess) {
+            switch (U->prec * 100 + U->recon) {
+            case F64 * 100 + 18: e = force_push_launch<F64, 18>(U, X_e_dev, Ye, Zo, Bo, k2, mode, sch, F_dev, Hf, Hb, s); break;
+            case F64 * 100 + 12: e = force_push_launch<F64, 12>(U, X_e_dev, Ye, Zo, Bo, k2, mode, sch, F_dev, Hf, Hb, s); break;
+            case F32 * 100 + 18: e = force_push_launch<F32, 18>(U, X_e_dev, Ye, Zo, Bo, k2, mode, sch, F_dev, Hf, Hb, s); break;
+            case F32 * 100 + 12: e = force_push_launch<F32, 12>(U, X_e_dev, Ye, Zo, Bo, k2, mode, sch, F_dev, Hf, Hb, s); break;
+            default: e = cudaErrorInvalidValue;
+            }
+        }
+        if (e == cudaSuccess && scheme == TM_FORCE_HALO) {
+            k_force_halo_sum<<<unsigned((nF + 255) / 256), 256, 0, s>>>(nF, Hf, Hb, F_dev);
+            e = cudaGetLastError();
+        }
     }
     if (e != cudaSuccess) {
         ctx->err = std::string("tm_force: ") + cudaGetErrorString(e);
         return TM_ERR_CUDA;
     }
     return TM_OK;
+}
+
+extern "C" tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa,
+                              double mu, int mode, void *stream)
+{
+    return tm_force_ex(ctx, U, F_dev, X_e_dev, kappa, mu, mode, TM_FORCE_OWNER, stream);
 }

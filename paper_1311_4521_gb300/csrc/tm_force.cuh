@@ -54,21 +54,95 @@ template <typename R> TM_HD void apply_g5(Spinor<R> &s)
 
 enum { FORCE_SU3 = 0, FORCE_GRAD = 1 };
 
+// The anti-Hermitian part A = W - W^dag of a 3x3 matrix W, kept as its three
+// upper off-diagonal entries and the imaginary parts of W's diagonal
+// (A_aa = 2 i Im W_aa; A_ca = -conj(A_ac)).  The force needs only this part,
+// so W itself is never formed.
+template <typename R> struct AntiH {
+    cpx<R> off[3];  // A_01, A_02, A_12
+    R dg[3];        // Im W_00, Im W_11, Im W_22
+};
+
+template <typename R> TM_HD void antih_zero(AntiH<R> &A)
+{
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        A.off[q] = {R(0), R(0)};
+        A.dg[q] = R(0);
+    }
+}
+
+// A += SGN * AH(sum_b x_b y_b^dag) for two colour vectors per argument:
+// (x y^dag)_ac - conj((x y^dag)_ca) = x_a conj(y_c) - conj(x_c) y_a.
+template <int SGN, typename R> TM_HD void antih_outer(const Half<R> &x, const Half<R> &y, AntiH<R> &A)
+{
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int a = q == 2 ? 1 : 0, c = q == 0 ? 1 : 2;
+        cpx<R> acc = A.off[q];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const cpx<R> xa = x[b][a], xc = x[b][c];
+            if (SGN > 0) {
+                acc = cjmadd(y[b][c], xa, acc);
+                acc = cjmadd(cpx<R>{-xc.re, -xc.im}, y[b][a], acc);
+            } else {
+                acc = cjmadd(y[b][c], cpx<R>{-xa.re, -xa.im}, acc);
+                acc = cjmadd(xc, y[b][a], acc);
+            }
+        }
+        A.off[q] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R d = A.dg[a];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const cpx<R> xa = x[b][a], ya = y[b][a];
+            if (SGN > 0) d = d + xa.im * ya.re - xa.re * ya.im;  // Im(x_a conj(y_a))
+            else d = d - xa.im * ya.re + xa.re * ya.im;
+        }
+        A.dg[a] = d;
+    }
+}
+
+// out = c TA(W), TA(W) = (W - W^dag)/2 - tr((W - W^dag)/2)/3, from A = AH(W).
+// The result is anti-Hermitian exactly (the lower half is the negated
+// conjugate of the upper half, the diagonal real parts are zero).
+template <typename R> TM_HD void antih_store(const AntiH<R> &A, R c, Mat<R> &out)
+{
+    const R h = R(0.5) * c;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int a = q == 2 ? 1 : 0, b = q == 0 ? 1 : 2;
+        const cpx<R> v = {h * A.off[q].re, h * A.off[q].im};
+        out[a][b] = v;
+        out[b][a] = {-v.re, v.im};
+    }
+    const R t = (A.dg[0] + A.dg[1] + A.dg[2]) / R(3);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a][a] = {R(0), c * (A.dg[a] - t)};
+}
+
 // Force (mode FORCE_SU3) or complex gradient (FORCE_GRAD) of the link U_mu(x)
 // from the fields at its two ends; sgn is the boundary sign of the link.
+// SU3: W = U M1 - M2 U^dag = sum_b (U h_b) k_b^dag - h'_b (U k'_b)^dag with
+// h, k the (1 - gamma_mu) halves of R(x+mu), L(x) and h', k' the
+// (1 + gamma_mu) halves of R(x), L(x+mu): two link-times-half-spinor
+// products instead of two 3x3 matrix products.
 template <int MU, typename R>
 TM_HD void force_link(const Link<R> &u, const Spinor<R> &Rx, const Spinor<R> &Lx, const Spinor<R> &Rxp,
                       const Spinor<R> &Lxp, R kappa2, R sgn, int mode, Mat<R> &out)
 {
     Half<R> h, k;
-    Mat<R> M1, M2;
-    project<MU, -1>(Rxp, h);
-    project<MU, -1>(Lx, k);
-    outer(h, k, M1);
-    project<MU, +1>(Rx, h);
-    project<MU, +1>(Lxp, k);
-    outer(h, k, M2);
     if (mode == FORCE_GRAD) {
+        Mat<R> M1, M2;
+        project<MU, -1>(Rxp, h);
+        project<MU, -1>(Lx, k);
+        outer(h, k, M1);
+        project<MU, +1>(Rx, h);
+        project<MU, +1>(Lxp, k);
+        outer(h, k, M2);
         const R c = R(2) * kappa2 * sgn;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -76,34 +150,74 @@ TM_HD void force_link(const Link<R> &u, const Spinor<R> &Rx, const Spinor<R> &Lx
             for (int b = 0; b < 3; ++b) out[a][b] = c * (conj(M1[b][a]) + M2[a][b]);
         return;
     }
-    // W = U M1 - M2 U^dag
-    Mat<R> W;
+    AntiH<R> A;
+    antih_zero(A);
+    Half<R> uv;
+    project<MU, -1>(Rxp, h);
+    link_mul<false>(u, h, uv);
+    project<MU, -1>(Lx, k);
+    antih_outer<+1>(uv, k, A);
+    project<MU, +1>(Lxp, k);
+    link_mul<false>(u, k, uv);
+    project<MU, +1>(Rx, h);
+    antih_outer<-1>(h, uv, A);
+    antih_store(A, -kappa2 * sgn, out);  // F = -kappa^2 s TA(W)
+}
+
+// The two halves of the link force for the push schemes: the forward part
+// (from the hop x -> x+mu, computed at the link's base x from R(x+mu), L(x))
+// and the backward part (from the hop x+mu -> x, computed at its tip x+mu
+// from R(x), L(x+mu)).  F = fwd + bwd; TA is linear, so
+//   FORCE_SU3:  fwd = -kappa^2 s TA(U M1),  bwd = +kappa^2 s TA(M2 U^dag)
+//   FORCE_GRAD: fwd = 2 kappa^2 s M1^dag,   bwd = 2 kappa^2 s M2.
+template <int MU, typename R>
+TM_HD void force_part_fwd(const Link<R> &u, const Spinor<R> &Rxp, const Spinor<R> &Lx, R kappa2, R sgn, int mode,
+                          Mat<R> &out)
+{
+    Half<R> h, k;
+    project<MU, -1>(Rxp, h);
+    project<MU, -1>(Lx, k);
+    if (mode == FORCE_GRAD) {
+        Mat<R> M1;
+        outer(h, k, M1);
+        const R c = R(2) * kappa2 * sgn;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            cpx<R> acc = {R(0), R(0)};
+            for (int b = 0; b < 3; ++b) out[a][b] = c * conj(M1[b][a]);
+        return;
+    }
+    AntiH<R> A;
+    antih_zero(A);
+    Half<R> uv;
+    link_mul<false>(u, h, uv);
+    antih_outer<+1>(uv, k, A);
+    antih_store(A, -kappa2 * sgn, out);
+}
+
+template <int MU, typename R>
+TM_HD void force_part_bwd(const Link<R> &u, const Spinor<R> &Rx, const Spinor<R> &Lxp, R kappa2, R sgn, int mode,
+                          Mat<R> &out)
+{
+    Half<R> h, k;
+    project<MU, +1>(Rx, h);
+    project<MU, +1>(Lxp, k);
+    if (mode == FORCE_GRAD) {
+        Mat<R> M2;
+        outer(h, k, M2);
+        const R c = R(2) * kappa2 * sgn;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                acc = cmadd(u[a][c], M1[c][b], acc);
-                acc = acc - M2[a][c] * conj(u[b][c]);
-            }
-            W[a][b] = acc;
-        }
-    // F = -kappa^2 s TA(W)
-    const R c = -kappa2 * sgn;
-    cpx<R> tr = {R(0), R(0)};
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) tr = tr + R(0.5) * (W[a][a] - conj(W[a][a]));
-    const cpx<R> tr3 = {R(0), tr.im / R(3)};
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            cpx<R> v = R(0.5) * (W[a][b] - conj(W[b][a]));
-            if (a == b) v = v - tr3;
-            out[a][b] = c * v;
-        }
+            for (int b = 0; b < 3; ++b) out[a][b] = c * M2[a][b];
+        return;
+    }
+    AntiH<R> A;
+    antih_zero(A);
+    Half<R> uv;
+    link_mul<false>(u, k, uv);
+    antih_outer<+1>(h, uv, A);
+    antih_store(A, kappa2 * sgn, out);
 }
 
 // Lexicographic index of the site with even-odd index i and parity p.

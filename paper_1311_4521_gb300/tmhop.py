@@ -23,6 +23,7 @@ TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_NOT_CONVERGED, TM_ERR_NONFINITE, TM_ERR_T
 TM_F64, TM_F32, TM_F16, TM_F64X = 0, 1, 2, 3
 TM_EO, TM_OE = 0, 1
 TM_FORCE_SU3, TM_FORCE_GRAD = 0, 1
+TM_FORCE_OWNER, TM_FORCE_ATOMIC, TM_FORCE_HALO = 0, 1, 2
 PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16, "f64x": TM_F64X}
 
 
@@ -73,6 +74,7 @@ def _load() -> ctypes.CDLL:
         "tm_cg_QdagQ": ([P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
         "tm_ctx_set_autotune": ([P, I], I),
         "tm_force": ([P, P, P, P, D, D, I, P], I),
+        "tm_force_ex": ([P, P, P, P, D, D, I, I, P], I),
         "tm_solve_eo": ([P, P, P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
         "tm_Qtm_batch": ([P, I, P, P, P, D, D, I, P], I),
         "tm_cg_QdagQ_batch": ([P, I, P, P, P, P, ctypes.POINTER(CgParams), P, P], I),
@@ -198,6 +200,11 @@ def tm_solve_eo(ctx, U_hi, U_lo, x_e, x_o, b_e, b_o, params: CgParams, stream=No
 
 def tm_force(ctx, U, F_dev, X_e_dev, kappa, mu, mode=TM_FORCE_SU3, stream=None):
     _check(ctx, lib.tm_force(ctx, U, _ptr(F_dev), _ptr(X_e_dev), float(kappa), float(mu), int(mode), _stream(stream)))
+
+
+def tm_force_ex(ctx, U, F_dev, X_e_dev, kappa, mu, mode=TM_FORCE_SU3, scheme=TM_FORCE_OWNER, stream=None):
+    _check(ctx, lib.tm_force_ex(ctx, U, _ptr(F_dev), _ptr(X_e_dev), float(kappa), float(mu), int(mode), int(scheme),
+                                _stream(stream)))
 
 
 def tm_ctx_set_autotune(ctx, on: bool) -> None:
@@ -334,11 +341,11 @@ class Context:
                                x_e, x_o, b_e, b_o, prm)
         return st, info.as_dict()
 
-    def force(self, U: Gauge, X_e, kappa, mu, mode=TM_FORCE_SU3) -> torch.Tensor:
+    def force(self, U: Gauge, X_e, kappa, mu, mode=TM_FORCE_SU3, scheme=TM_FORCE_OWNER) -> torch.Tensor:
         """Force (or complex gradient) of S = phi^dag (Q^dag Q)^-1 phi given packed X; (4, V, 3, 3) complex128."""
         V = 2 * U.vh
         F = torch.empty((4, V, 3, 3, 2), dtype=torch.float64, device=self.device)
-        tm_force(self.handle, U.handle, F, X_e, kappa, mu, mode)
+        tm_force_ex(self.handle, U.handle, F, X_e, kappa, mu, mode, scheme)
         return torch.view_as_complex(F)
 
     def Qtm_batch(self, gauges, outs, ins, kappa, mu, sign=1):

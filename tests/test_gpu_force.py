@@ -8,6 +8,10 @@
   X^dag Q^dag Q X: central steps of 1e-6 on 20 random (link, generator)
   pairs of an 8^4 lattice, and along one random su(3) direction of every
   link at once on 24^3x48.
+* the two push schemes of tm_force_ex (FP64 atomic adds, and private
+  forward/backward buffers summed by a second pass) against the oracle on
+  8^4 and on shapes with extent-2 directions and a ragged tail, bit-equal to
+  each other and, run twice, to themselves.
 * autograd: dS/dphi = 2X against finite differences (exact for a quadratic
   form), dS/dU against the oracle force, and the backward passes of the
   linear operators against the oracle's literal adjoints.
@@ -69,6 +73,65 @@ def test_gradient_mode_gives_the_force(ctx, small):
     g.close()
     Ud = torch.from_numpy(U).to(G.device)
     assert rel(autograd.su3_force(Ud, G).cpu().numpy(), Fs.cpu().numpy()) < 1e-13
+
+
+SCHEMES = ("atomic", "halo")
+
+
+def force_scheme(ctx, dims, U, X, prec, scheme, mode=0, bc=(-1, 1, 1, 1), k=0.16, mu=0.01):
+    from paper_1311_4521_gb300 import tmhop
+    g = ctx.gauge(dims, U, prec, RECON[prec], bc)
+    sch = {"owner": tmhop.TM_FORCE_OWNER, "atomic": tmhop.TM_FORCE_ATOMIC, "halo": tmhop.TM_FORCE_HALO}[scheme]
+    out = ctx.force(g, ctx.pack(X, prec), k, mu, mode, sch).cpu().numpy()
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_push_schemes_match_oracle(ctx, small, prec, mode):
+    dims, U, X = small
+    want = O.force(dims, U, X, 0.16, 0.01)
+    owner = force_scheme(ctx, dims, U, X, prec, "owner", mode)
+    got = {s: force_scheme(ctx, dims, U, X, prec, s, mode) for s in SCHEMES}
+    # two addends per entry onto zero: the order of the atomics cannot matter
+    assert np.array_equal(got["atomic"], got["halo"])
+    assert np.array_equal(got["atomic"], force_scheme(ctx, dims, U, X, prec, "atomic", mode))
+    assert rel(got["halo"], owner) < TOLF[prec]
+    if mode == 0:
+        assert rel(got["halo"], want) < TOLF[prec]
+    else:
+        from paper_1311_4521_gb300 import autograd
+        Ud = torch.from_numpy(U)
+        Fs = autograd.su3_force(Ud, torch.from_numpy(got["halo"])).numpy()
+        assert rel(Fs, want) < TOLF[prec]
+
+
+@pytest.mark.parametrize("dims,bc", [((2, 2, 2, 2), (-1, 1, 1, 1)), ((6, 4, 2, 10), (-1, 1, -1, 1)),
+                                     ((10, 6, 4, 2), (1, -1, 1, -1))])
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_push_schemes_ragged(ctx, dims, bc, scheme):
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, 11, "random")
+    X = F.gaussian_spinor(vh, 11, 5)
+    want = O.force(dims, U, X, 0.1394, 0.0015, bc=bc)
+    got = force_scheme(ctx, dims, U, X, "f64", scheme, bc=bc, k=0.1394, mu=0.0015)
+    assert rel(got, want) < 1e-12
+
+
+def test_push_scheme_errors(ctx, small):
+    from paper_1311_4521_gb300 import tmhop
+    dims, U, X = small
+    g = ctx.gauge(dims, U, "f16", 12)
+    with pytest.raises(tmhop.TmError) as e:
+        ctx.force(g, ctx.pack(X, "f16"), 0.16, 0.01, 0, tmhop.TM_FORCE_ATOMIC)
+    assert e.value.status == tmhop.TM_ERR_UNSUPPORTED
+    g.close()
+    g = ctx.gauge(dims, U, "f64", 18)
+    with pytest.raises(tmhop.TmError) as e:
+        ctx.force(g, ctx.pack(X, "f64"), 0.16, 0.01, 0, 7)
+    assert e.value.status == tmhop.TM_ERR_ARG
+    g.close()
 
 
 def solve(ctx, dims, U, phi, kappa, mu, tol, prec="f64", with_ax=False):
