@@ -56,9 +56,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # (profiles/k_hop_f64_24x24x24x48_full.md, profiles/k_hop_dram_f32_f16_32x32x32x64.md),
 # scaled to a 32^3x64 launch by the site count, valid only for the kernel
 # sources they were taken from (hash of csrc/tm_device.cuh + csrc/tm_kernels.cu).
-TRAFFIC = {"src": "3543dd0ab4c97a29",
-           "per_site": {("f64", 18): (512741120 + 34648832) / 331776, ("f64x", 18): (513134592 + 34616832) / 331776,
-                        ("f32", 12): (607335936 + 69721344) / 1048576, ("f16", 12): (312124160 + 28563456) / 1048576}}
+TRAFFIC = {"src": "88f9a74531a64db5",
+           "per_site": {("f64", 18): (513052928 + 34657792) / 331776, ("f64x", 18): (512999936 + 33824000) / 331776,
+                        ("f32", 12): (607398912 + 69914880) / 1048576, ("f16", 12): (312123648 + 28238848) / 1048576}}
 
 
 def kernel_source_hash() -> str:
@@ -301,39 +301,32 @@ def gpu_arm(args) -> None:
         gx.close()
         del sx, dx
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies in the timed region
+    # ---- end to end through the C ABI with host buffers (pinned), copies in the timed region:
+    # tm_Qtm_host over `ne` host-resident fields, each copied in, packed,
+    # multiplied, unpacked and copied out (copies of neighbouring fields
+    # overlap the kernels on two copy streams)
     e2e = None
     if not args.no_e2e:
         host_in = torch.from_numpy(np.ascontiguousarray(psi)).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        dev_can = torch.empty(host_in.shape, dtype=torch.complex128, device="cuda")
-        dev_out = torch.empty_like(dev_can)
         ne = max(1, min(args.steps, args.e2e_steps))
-
-        def e2e_step():
-            dev_can.copy_(host_in, non_blocking=True)
-            tmhop.tm_spinor_pack(ctx.handle, vh, torch.view_as_real(dev_can), src, tmhop.PREC[prec])
-            ctx.Qtm(g, dst, src, KAPPA, MU)
-            tmhop.tm_spinor_unpack(ctx.handle, vh, dst, torch.view_as_real(dev_out), tmhop.PREC[prec])
-            host_out.copy_(dev_out, non_blocking=True)
-
-        for _ in range(args.warmup):
-            e2e_step()
+        stream = torch.cuda.current_stream()
+        for _ in range(max(1, args.warmup // 4)):
+            tmhop.tm_Qtm_host(ctx.handle, g.handle, [host_out] * 4, [host_in] * 4, KAPPA, MU, 1, stream.cuda_stream)
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
-        s0.record()
-        for _ in range(ne):
-            e2e_step()
-        s1.record()
+        s0.record(stream)
+        tmhop.tm_Qtm_host(ctx.handle, g.handle, [host_out] * ne, [host_in] * ne, KAPPA, MU, 1, stream.cuda_stream)
+        s1.record(stream)
         torch.cuda.synchronize()
         barrier()
         e2e_ms = allmax(s0.elapsed_time(s1)) / ne
         nbytes = host_in.numel() * 16
         e2e = {"value": round(world * vh * ab["qtm"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e2e_ms, 4),
-               "steps": ne, "gpu_launches_per_step": 4}
-        del host_in, host_out, dev_can, dev_out
+               "steps": ne, "gpu_launches_per_step": 4, "api": "tm_Qtm_host (pinned host fields, pipelined copies)"}
+        del host_in, host_out
     links_gb = tmhop.tm_gauge_bytes(g.handle) / 1e9
     g.close()
 
@@ -453,7 +446,7 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier, keep_host=False):
     bx = ctx.pack(b, "f64x")
     x = ctx.empty(vh, "f64")
     out = {"lattice": list(dims), "tol": 1e-10, "kappa": KAPPA, "mu": MU, "reliable_every": 50,
-           "reliable_delta": 0.1, "source": "Gaussian, seed 2013", "time": "CUDA events around one warm solve"}
+           "reliable_delta": args.cg_delta, "source": "Gaussian, seed 2013", "time": "CUDA events around one warm solve"}
     stream = torch.cuda.current_stream()
     runs = (("fp64", gh, bd, None), ("mixed_f32", gh, bd, lo["mixed_f32"]), ("mixed_f16", gh, bd, lo["mixed_f16"]),
             ("fp64x", gx, bx, None), ("mixed_f32_fp64x", gx, bx, lo["mixed_f32"]),
@@ -465,7 +458,7 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier, keep_host=False):
             barrier()
             torch.cuda.synchronize()
             e0.record(stream)
-            st, info = ctx.cg(ghi, x, bb, KAPPA, MU, 1e-10, 30000, gl, 50, True, 0.1)
+            st, info = ctx.cg(ghi, x, bb, KAPPA, MU, 1e-10, 30000, gl, 50, True, args.cg_delta)
             e1.record(stream)
             torch.cuda.synchronize()
         sec = allmax(e0.elapsed_time(e1) / 1e3)
@@ -751,6 +744,8 @@ def main() -> None:
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--only", choices=["batch-qtm", "cg", "force", "solve"], default=None,
                     help="run one section alone (for profiling captures)")
+    ap.add_argument("--cg-delta", type=float, default=0.1,
+                    help="reliable-update threshold of the mixed-precision solvers (residual drop factor)")
     ap.add_argument("--force-scheme", choices=["owner", "atomic", "halo"], default="owner",
                     help="force assembly for --only force")
     ap.add_argument("--cg-lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=(48, 48, 48, 96))

@@ -24,7 +24,9 @@
  *     lex/2.
  *   - Pointers named *_dev are device memory of the context's device,
  *     owned by the caller, 16-byte aligned, and not overlapping unless
- *     stated.  Host pointers are named *_host.
+ *     stated; a null or misaligned field pointer gives TM_ERR_ARG (the
+ *     kernels use 16-byte vector accesses).  Host pointers are named
+ *     *_host.
  *   - "Packed" spinor fields are the library's storage of one parity in a
  *     given precision (component-major, see tm_spinor_bytes); they are
  *     produced by tm_spinor_pack and read back by tm_spinor_unpack.
@@ -218,6 +220,24 @@ enum { TM_FORCE_SU3 = 0,    /* F in su(3): U -> exp(eps T) U changes S by eps <T
  * (no atomics).  Scratch is owned by ctx. */
 tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa, double mu,
                    int mode, void *stream);
+
+/* ---- host-resident fields --------------------------------------------------- */
+
+/* Q_tm (sign as in tm_Qtm) on n one-parity fields in host memory:
+ * out_host[k] = Q in_host[k], each a complex double [Vh][4][3] array (the
+ * layout tm_spinor_pack reads).  The fields go through two device staging
+ * slots in U's storage precision, pipelined: field k+1 is copied to the
+ * device and field k-1 back to the host on two copy streams owned by the
+ * context while field k is packed, multiplied and unpacked on `stream`.
+ * Host buffers should be pinned (cudaHostAlloc, cudaHostRegister) for the
+ * copies to overlap the kernels; pageable memory works but serialises.  No
+ * output may be one of the inputs (TM_ERR_ARG), and no buffers may overlap.
+ * Synchronous: returns when every output is in host memory.  Device memory:
+ * two slots of two canonical and two packed fields, kept by the context
+ * (grow-only), plus tm_Qtm's scratch.  The paper has no counterpart; this is
+ * the entry point for callers whose data is in host memory. */
+tm_status tm_Qtm_host(tm_ctx *ctx, const tm_gauge *U, int n, double *const *out_host, const double *const *in_host,
+                      double kappa, double mu, int sign, void *stream);
 
 /* How tm_force_ex assembles the per-link force.  Every link's force has two
  * parts, one from each hop that uses the link; the paper (Sec. 2.4) weighs

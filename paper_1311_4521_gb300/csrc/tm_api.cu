@@ -86,6 +86,9 @@ void tm_ctx_destroy(tm_ctx *ctx)
     if (!ctx) return;
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+    if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     delete ctx;
 }
 
@@ -125,7 +128,7 @@ tm_status tm_spinor_pack(tm_ctx *ctx, long vh, const double *in_dev, void *out_d
     if (!ctx) return TM_ERR_ARG;
     if (vh < 0 || vh >= (1L << 31)) return fail(ctx, TM_ERR_ARG, "tm_spinor_pack: bad site count");
     if (!valid_prec(prec)) return fail(ctx, TM_ERR_ARG, "tm_spinor_pack: bad precision");
-    if (vh > 0 && (!in_dev || !out_dev)) return fail(ctx, TM_ERR_ARG, "tm_spinor_pack: null pointer");
+    if (vh > 0 && (bad_ptr(in_dev) || bad_ptr(out_dev))) return fail(ctx, TM_ERR_ARG, "tm_spinor_pack: null or misaligned pointer");
     TM_CUDA(ctx, launch_pack_spinor(unsigned(vh), prec, in_dev, out_dev, (cudaStream_t)stream));
     return TM_OK;
 }
@@ -135,7 +138,7 @@ tm_status tm_spinor_unpack(tm_ctx *ctx, long vh, const void *in_dev, double *out
     if (!ctx) return TM_ERR_ARG;
     if (vh < 0 || vh >= (1L << 31)) return fail(ctx, TM_ERR_ARG, "tm_spinor_unpack: bad site count");
     if (!valid_prec(prec)) return fail(ctx, TM_ERR_ARG, "tm_spinor_unpack: bad precision");
-    if (vh > 0 && (!in_dev || !out_dev)) return fail(ctx, TM_ERR_ARG, "tm_spinor_unpack: null pointer");
+    if (vh > 0 && (bad_ptr(in_dev) || bad_ptr(out_dev))) return fail(ctx, TM_ERR_ARG, "tm_spinor_unpack: null or misaligned pointer");
     TM_CUDA(ctx, launch_unpack_spinor(unsigned(vh), prec, in_dev, out_dev, (cudaStream_t)stream));
     return TM_OK;
 }
@@ -144,7 +147,7 @@ tm_status tm_gauge_create(tm_ctx *ctx, const int dims[4], const double *U_dev, i
                           const int bc[4], void *stream, tm_gauge **out)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!out || !dims || !U_dev || !bc) return fail(ctx, TM_ERR_ARG, "tm_gauge_create: null pointer");
+    if (!out || !dims || bad_ptr(U_dev) || !bc) return fail(ctx, TM_ERR_ARG, "tm_gauge_create: null or misaligned pointer");
     *out = nullptr;
     if (!valid_prec(prec)) return fail(ctx, TM_ERR_ARG, "tm_gauge_create: bad precision");
     if (reconstruct != 12 && reconstruct != 18) return fail(ctx, TM_ERR_ARG, "tm_gauge_create: reconstruct must be 12 or 18");
@@ -191,7 +194,7 @@ tm_status tm_hopping_eo(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const voi
                         void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!U || !out_dev || !in_dev) return fail(ctx, TM_ERR_ARG, "tm_hopping_eo: null pointer");
+    if (!U || bad_ptr(out_dev) || bad_ptr(in_dev)) return fail(ctx, TM_ERR_ARG, "tm_hopping_eo: null or misaligned pointer");
     if (dir != TM_EO && dir != TM_OE) return fail(ctx, TM_ERR_ARG, "tm_hopping_eo: dir must be TM_EO or TM_OE");
     if (out_dev == in_dev) return fail(ctx, TM_ERR_ARG, "tm_hopping_eo: out and in must not overlap");
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, dagger != 0, dir, U->links, in_dev, out_dev, nullptr,
@@ -203,7 +206,7 @@ tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in
                  int sign, void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!U || !out_e_dev || !in_e_dev) return fail(ctx, TM_ERR_ARG, "tm_Qtm: null pointer");
+    if (!U || bad_ptr(out_e_dev) || bad_ptr(in_e_dev)) return fail(ctx, TM_ERR_ARG, "tm_Qtm: null or misaligned pointer");
     if (sign != 1 && sign != -1) return fail(ctx, TM_ERR_ARG, "tm_Qtm: sign must be +1 or -1");
     if (out_e_dev == in_e_dev) return fail(ctx, TM_ERR_ARG, "tm_Qtm: out and in must not overlap");
     void *tmp = nullptr;
@@ -213,10 +216,10 @@ tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in
     cudaStream_t s = (cudaStream_t)stream;
     tm_trace_mark(ctx, 0, s);
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, in_e_dev, tmp, nullptr,
-                            coef_qtm_a(mut), s, 128));
+                            coef_qtm_a_scaled(kappa, mut), s, 128));
     tm_trace_mark(ctx, 1, s);
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, tmp, out_e_dev, in_e_dev,
-                            coef_qtm_b(kappa, mut), s, 128));
+                            coef_qtm_b_unit(mut), s, 128));
     tm_trace_mark(ctx, 2, s);
     return TM_OK;
 }

@@ -429,7 +429,7 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
         if (h->prec != prec || h->recon != recon)
             return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_Qtm_batch: all gauge handles need the same precision and reconstruction");
     for (int k = 0; k < nsys; ++k) {
-        if (!out_e[k] || !in_e[k] || out_e[k] == in_e[k]) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad field pointer");
+        if (bad_ptr(out_e[k]) || bad_ptr(in_e[k]) || out_e[k] == in_e[k]) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad field pointer");
     }
     // workspace: odd temporaries, system table, group table
     size_t need = 0;
@@ -472,9 +472,9 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: setup");
     const double mut = 2.0 * kappa * mu * sign;
     tm_trace_mark(ctx, 0, s);
-    e = bhop(prec, recon, t, dsys, 1, R_IN, R_T, -1, coef_qtm_a(mut), false, 0, s);
+    e = bhop(prec, recon, t, dsys, 1, R_IN, R_T, -1, coef_qtm_a_scaled(kappa, mut), false, 0, s);
     tm_trace_mark(ctx, 1, s);
-    if (e == cudaSuccess) e = bhop(prec, recon, t, dsys, 0, R_T, R_OUT, R_IN, coef_qtm_b(kappa, mut), false, 0, s);
+    if (e == cudaSuccess) e = bhop(prec, recon, t, dsys, 0, R_T, R_OUT, R_IN, coef_qtm_b_unit(mut), false, 0, s);
     tm_trace_mark(ctx, 2, s);
     if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: launch");
     // the tables live in scratch: keep them until the launches have read them
@@ -507,7 +507,7 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
             lo[g] = l;
             if (memcmp(l->dims, handles[g]->dims, sizeof l->dims) || memcmp(l->bc, handles[g]->bc, sizeof l->bc))
                 return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi and U_lo describe different lattices");
-            if (!x_dev[k] || !b_dev[k] || x_dev[k] == b_dev[k]) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad field pointer");
+            if (bad_ptr(x_dev[k]) || bad_ptr(b_dev[k]) || x_dev[k] == b_dev[k]) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad field pointer");
         }
     }
     for (size_t g = 0; g < handles.size(); ++g)
@@ -615,10 +615,10 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
     auto hop_tile = [&](const HopTable &t) { return unsigned(t.nrb > 1 ? BT / t.nrb : BT); };
     // ax = Q^dag Q x in FP64 for the systems the gate lets through
     auto qdagq_hi = [&](int gate, cudaStream_t q) {
-        cudaError_t r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_X, R_THI, -1, coef_qtm_a(mut), false, gate, q);
-        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_QHI, R_X, coef_qtm_b(kappa, mut), false, gate, q);
-        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_QHI, R_THI, -1, coef_qtm_a(-mut), false, gate, q);
-        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_AX, R_QHI, coef_qtm_b(kappa, -mut), false, gate, q);
+        cudaError_t r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_X, R_THI, -1, coef_qtm_a_scaled(kappa, mut), false, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_QHI, R_X, coef_qtm_b_unit(mut), false, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_QHI, R_THI, -1, coef_qtm_a_scaled(kappa, -mut), false, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_AX, R_QHI, coef_qtm_b_unit(-mut), false, gate, q);
         return r;
     };
     auto residual = [&](int gate, cudaStream_t q) {
@@ -638,11 +638,11 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
         return r;
     };
     auto iteration = [&](cudaStream_t q) {
-        cudaError_t r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_P, R_T, -1, coef_qtm_a(mut), false, 1, q);
-        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_Q, R_P, coef_qtm_b(kappa, mut), true, 1, q);
+        cudaError_t r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_P, R_T, -1, coef_qtm_a_scaled(kappa, mut), false, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_Q, R_P, coef_qtm_b_unit(mut), true, 1, q);
         if (r == cudaSuccess) r = finish(hop_tile(B.lo), FIN_PAP, 1, q);
-        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_Q, R_T, -1, coef_qtm_a(-mut), false, 1, q);
-        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_AP, R_Q, coef_qtm_b(kappa, -mut), false, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_Q, R_T, -1, coef_qtm_a_scaled(kappa, -mut), false, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_AP, R_Q, coef_qtm_b_unit(-mut), false, 1, q);
         if (r != cudaSuccess) return r;
         if (B.P == F64) k_batch_update<F64, F64><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);
         else if (B.P == F32) k_batch_update<F32, F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);

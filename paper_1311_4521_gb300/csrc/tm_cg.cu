@@ -302,10 +302,10 @@ cudaError_t qdagq(const tm_gauge *U, double kappa, double mu, const void *in, vo
                   const Work &w, int gate, cudaStream_t st)
 {
     double mut = 2.0 * kappa * mu;
-    cudaError_t e = hop(U, 1, in, t, nullptr, coef_qtm_a(mut), false, w, gate, st);
-    if (e == cudaSuccess) e = hop(U, 0, t, q, in, coef_qtm_b(kappa, mut), norm, w, gate, st);
-    if (e == cudaSuccess) e = hop(U, 1, q, t, nullptr, coef_qtm_a(-mut), false, w, gate, st);
-    if (e == cudaSuccess) e = hop(U, 0, t, out, q, coef_qtm_b(kappa, -mut), false, w, gate, st);
+    cudaError_t e = hop(U, 1, in, t, nullptr, coef_qtm_a_scaled(kappa, mut), false, w, gate, st);
+    if (e == cudaSuccess) e = hop(U, 0, t, q, in, coef_qtm_b_unit(mut), norm, w, gate, st);
+    if (e == cudaSuccess) e = hop(U, 1, q, t, nullptr, coef_qtm_a_scaled(kappa, -mut), false, w, gate, st);
+    if (e == cudaSuccess) e = hop(U, 0, t, out, q, coef_qtm_b_unit(-mut), false, w, gate, st);
     return e;
 }
 
@@ -448,7 +448,7 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
 {
     auto t_start = std::chrono::steady_clock::now();
     if (!ctx) return TM_ERR_ARG;
-    if (!U_hi || !x_dev || !b_dev || !prm) return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: null pointer");
+    if (!U_hi || bad_ptr(x_dev) || bad_ptr(b_dev) || !prm) return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: null or misaligned pointer");
     if (U_hi->prec != TM_F64 && U_hi->prec != TM_F64X)
         return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi must be an FP64 or FP64X handle");
     if (!U_lo) U_lo = U_hi;

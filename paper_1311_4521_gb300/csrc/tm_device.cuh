@@ -24,6 +24,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "tm_dd.cuh"
 
@@ -646,6 +647,108 @@ TM_HD void hop_dir(const Geom &g, const Nbrs &n, const Src &src, const void *in,
     }
 }
 
+// ---------------------------------------------------------------- FP64 pairs
+// FP64 runs at 1/64 of the FP32 rate here, so the FP64 hop is bound by its
+// FP64 operation count, not by memory.  The two hops of one direction share
+// their spin reconstruction: with rf = w_f U_mu(x) h_f and
+// rb = w_b U_mu(x-mu)^dag h_b (w the boundary signs), the direction adds
+// rf + rb to the upper spins and SF A_mu^dag (rf - rb) to the lower ones.
+// The boundary signs are folded into h by flipping sign bits (integer
+// operations), the backward product's sums start from -rf so that
+// d = rb - rf comes out of the same fused multiply-adds, and then
+// upper += 2 rf + d, lower += SB A_mu^dag d: 36 FP64 operations per
+// direction for reconstruction and accumulation instead of 48 (24 for the
+// first direction, while the accumulator is still zero).
+TM_HD double flip_sign(double x, unsigned long long m)
+{
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)m);
+#else
+    unsigned long long b;
+    memcpy(&b, &x, 8);
+    b ^= m;
+    memcpy(&x, &b, 8);
+    return x;
+#endif
+}
+
+TM_HD void flip_sign(Half<double> &h, bool neg)
+{
+    const unsigned long long m = neg ? 0x8000000000000000ull : 0ull;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[s][c] = {flip_sign(h[s][c].re, m), flip_sign(h[s][c].im, m)};
+}
+
+// r = U h - sub (dag = false) or U^dag h - sub (dag = true)
+template <bool DAG, typename R>
+TM_HD void link_mul_minus(const Link<R> &u, const Half<R> &h, const Half<R> &sub, Half<R> &r)
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cpx<R> acc = {-sub[s][a].re, -sub[s][a].im};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) acc = DAG ? cjmadd(u[b][a], h[s][b], acc) : cmadd(u[a][b], h[s][b], acc);
+            r[s][a] = acc;
+        }
+}
+
+// the lower-spin term S A_mu^dag d for lower spin 2 + k
+template <int MU, int S, typename R> TM_HD cpx<R> lower_term(const Half<R> &d, int k, int c)
+{
+    cpx<R> v;
+    if (MU == 0) v = -d[k][c];                      // A_0^dag d = -(d0, d1)
+    else if (MU == 1) v = ti(d[1 - k][c]);          // A_1^dag d = (i d1, i d0)
+    else if (MU == 2) v = k == 0 ? d[1][c] : -d[0][c];  // A_2^dag d = (d1, -d0)
+    else v = k == 0 ? ti(d[0][c]) : -ti(d[1][c]);   // A_3^dag d = (i d0, -i d1)
+    return S > 0 ? v : -v;
+}
+
+template <int P, bool DAG, int MU, bool FIRST, class Src>
+TM_HD void hop_dir_pair(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<double> &acc)
+{
+    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
+    constexpr int SB = -SF;
+    Half<double> rf, d;
+    {
+        Spinor<double> s;
+        Half<double> h;
+        Link<double> u;
+        SpinorIO<P>::load_raw(in, g.vh, n.fwd[MU], s);
+        project<MU, SF>(s, h);
+        flip_sign(h, n.wf[MU] && g.anti[MU]);
+        src.template fwd<MU>(n, u);
+        link_mul<false>(u, h, rf);
+    }
+    {
+        Spinor<double> s;
+        Half<double> h;
+        Link<double> u;
+        SpinorIO<P>::load_raw(in, g.vh, n.bwd[MU], s);
+        project<MU, SB>(s, h);
+        flip_sign(h, n.wb[MU] && g.anti[MU]);
+        src.template bwd<MU>(n, u);
+        link_mul_minus<true>(u, h, rf, d);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cpx<double> lo = lower_term<MU, SB>(d, k, c);
+            if (FIRST) {
+                acc[k][c] = {2.0 * rf[k][c].re + d[k][c].re, 2.0 * rf[k][c].im + d[k][c].im};
+                acc[2 + k][c] = lo;
+            } else {
+                acc[k][c] = {(acc[k][c].re + 2.0 * rf[k][c].re) + d[k][c].re,
+                             (acc[k][c].im + 2.0 * rf[k][c].im) + d[k][c].im};
+                acc[2 + k][c] = acc[2 + k][c] + lo;
+            }
+        }
+}
+
 // The 8 hops as a loop that is not unrolled, for double-float storage: its
 // arithmetic expands to so many FP32 instructions that the fully unrolled
 // stencil overflows the instruction cache (ncu: warps stalled on
@@ -715,6 +818,11 @@ TM_HD void hop_site_src(const Geom &g, const Nbrs &n, const Src &src, const void
         for (int c = 0; c < 3; ++c) acc[s][c] = {R(0), R(0)};
     if constexpr (P == F64X) {
         hop_site_rolled<P, DAG>(g, n, src, in, acc);
+    } else if constexpr (P == F64) {
+        hop_dir_pair<P, DAG, 0, true>(g, n, src, in, acc);
+        hop_dir_pair<P, DAG, 1, false>(g, n, src, in, acc);
+        hop_dir_pair<P, DAG, 2, false>(g, n, src, in, acc);
+        hop_dir_pair<P, DAG, 3, false>(g, n, src, in, acc);
     } else {
         hop_dir<P, DAG, 0>(g, n, src, in, acc);
         hop_dir<P, DAG, 1>(g, n, src, in, acc);
@@ -737,14 +845,16 @@ TM_HD void hop_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, R
 // Site-local epilogue: out_u = a_u hop_u + b_u x_u, out_l = a_l hop_l + b_l x_l
 // (u = spins 0,1; l = spins 2,3).  With gamma5 = diag(1,1,-1,-1) this covers
 // the twisted-mass factors (1 +- i mut gamma5)^(+-1) and the final gamma5.
+// With `unit` set the hop term enters as +hop_u, -hop_l (no multiply).
 struct Coef {
     double d[8];  // au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im
     float f[8];   // the same, rounded once on the host for single-precision kernels
     float xh[8], xl[8];  // and as double-float pairs
+    int unit;            // a_u = 1, a_l = -1 exactly: the hop term is applied as a sign
     Coef() = default;
     __host__ __device__ Coef(double au_re, double au_im, double al_re, double al_im, double bu_re, double bu_im,
                              double bl_re, double bl_im)
-        : d{au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im}
+        : d{au_re, au_im, al_re, al_im, bu_re, bu_im, bl_re, bl_im}, unit(0)
     {
         for (int k = 0; k < 8; ++k) {
             f[k] = float(d[k]);
@@ -763,6 +873,17 @@ template <typename R> TM_HD void epilogue(const Coef &k, const Spinor<R> &hop, c
     const R z = R(0);
     cpx<R> au = {k.get(0, z), k.get(1, z)}, al = {k.get(2, z), k.get(3, z)};
     cpx<R> bu = {k.get(4, z), k.get(5, z)}, bl = {k.get(6, z), k.get(7, z)};
+    if (k.unit) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cpx<R> v = s < 2 ? hop[s][c] : -hop[s][c];
+                if (x) v = cmadd(s < 2 ? bu : bl, (*x)[s][c], v);
+                out[s][c] = v;
+            }
+        return;
+    }
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll

@@ -78,23 +78,21 @@ __device__ __forceinline__ void push_site(const Geom &g, int p, unsigned i, cons
     const size_t V = 2 * size_t(g.vh);
     const size_t lf = size_t(MU) * V + lex_of(g, p, i);              // link (mu, y)
     const size_t lb = size_t(MU) * V + lex_of(g, 1 - p, n.bwd[MU]);  // link (mu, y - mu)
+    if (SCHEME == PUSH_ATOMIC) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int k = 6 * a + 2 * b;
-            if (SCHEME == PUSH_ATOMIC) {
+            for (int b = 0; b < 3; ++b) {
+                const int k = 6 * a + 2 * b;
                 atomicAdd(F + lf * 18 + k, double(mf[a][b].re));
                 atomicAdd(F + lf * 18 + k + 1, double(mf[a][b].im));
                 atomicAdd(F + lb * 18 + k, double(mb[a][b].re));
                 atomicAdd(F + lb * 18 + k + 1, double(mb[a][b].im));
-            } else {
-                Hf[lf * 18 + k] = double(mf[a][b].re);
-                Hf[lf * 18 + k + 1] = double(mf[a][b].im);
-                Hb[lb * 18 + k] = double(mb[a][b].re);
-                Hb[lb * 18 + k + 1] = double(mb[a][b].im);
             }
-        }
+    } else {
+        store_mat(Hf + lf * 18, mf);
+        store_mat(Hb + lb * 18, mb);
+    }
 }
 
 template <int P, int RECON, int SCHEME>
@@ -150,8 +148,8 @@ extern "C" tm_status tm_force_ex(tm_ctx *ctx, const tm_gauge *U, double *F_dev, 
                                  double mu, int mode, int scheme, void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!U || !F_dev || !X_e_dev) {
-        ctx->err = "tm_force: null pointer";
+    if (!U || bad_ptr(F_dev) || bad_ptr(X_e_dev)) {
+        ctx->err = "tm_force: null or misaligned pointer";
         return TM_ERR_ARG;
     }
     if (mode != TM_FORCE_SU3 && mode != TM_FORCE_GRAD) {

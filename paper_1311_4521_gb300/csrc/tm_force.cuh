@@ -220,6 +220,19 @@ TM_HD void force_part_bwd(const Link<R> &u, const Spinor<R> &Rx, const Spinor<R>
     antih_store(A, kappa2 * sgn, out);
 }
 
+// One 3x3 complex matrix to its 144-byte slot of an FP64 force field, one
+// 16-byte (re, im) store per entry, evict-first (the field is written once).
+template <typename R> TM_HD void store_mat(double *o, const Mat<R> &m)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const double2 v = make_double2(double(m[a][b].re), double(m[a][b].im));
+            st_stream(reinterpret_cast<double2 *>(o) + 3 * a + b, v);
+        }
+}
+
 // Lexicographic index of the site with even-odd index i and parity p.
 TM_HD unsigned lex_of(const Geom &g, int p, unsigned i)
 {
@@ -260,14 +273,7 @@ TM_HD void force_site(const Geom &g, int p, unsigned i, const typename LinkIO<P,
     L::load(links + size_t(4 * p + MU) * L::NCHUNK * g.vh, g.vh, i, u);
     Mat<R> m;
     force_link<MU>(u, Rx, Lx, Rxp, Lxp, to_R<R>(kappa2), sgn, mode, m);
-    double *o = F + (size_t(MU) * 2 * g.vh + lex_of(g, p, i)) * 18;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            o[6 * a + 2 * b] = double(m[a][b].re);
-            o[6 * a + 2 * b + 1] = double(m[a][b].im);
-        }
+    store_mat(F + (size_t(MU) * 2 * g.vh + lex_of(g, p, i)) * 18, m);
 }
 
 }  // namespace twm

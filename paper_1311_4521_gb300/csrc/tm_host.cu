@@ -1,0 +1,138 @@
+// tm_host.cu -- Q_tm on spinor fields that live in host memory.
+//
+// A caller whose fields are in host memory (a host-side application, a
+// service that receives right-hand sides from elsewhere) pays, per
+// application, a host-to-device copy of the input, the operator and a
+// device-to-host copy of the result.  tm_Qtm_host takes a list of such
+// fields and pipelines them through two device staging slots: while field
+// k is packed, multiplied and unpacked on the compute stream, field k+1 is
+// copied in on one copy stream and field k-1 copied out on another.  With
+// pinned host memory the copies then hide behind the kernels.  Every copy is
+// one cudaMemcpyAsync of one contiguous field.
+#include <set>
+#include <string>
+
+#include "tm_internal.h"
+
+using namespace twm;
+
+namespace {
+
+tm_status host_fail(tm_ctx *ctx, tm_status st, const std::string &msg)
+{
+    ctx->err = msg;
+    return st;
+}
+
+size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
+
+tm_status grow_stage(tm_ctx *ctx, size_t bytes)
+{
+    if (ctx->stage_bytes >= bytes) return TM_OK;
+    if (ctx->stage) {
+        cudaError_t e = cudaFree(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        if (e != cudaSuccess) return host_fail(ctx, TM_ERR_CUDA, std::string("cudaFree(stage): ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc(&ctx->stage, bytes);
+    if (e != cudaSuccess) {
+        ctx->stage = nullptr;
+        return host_fail(ctx, TM_ERR_CUDA, std::string("cudaMalloc(stage): ") + cudaGetErrorString(e));
+    }
+    ctx->stage_bytes = bytes;
+    return TM_OK;
+}
+
+// The events of one call: per slot, "input copied", "input consumed by the
+// pack", "output unpacked", "output copied out".
+struct SlotEvents {
+    cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
+    cudaError_t create()
+    {
+        for (int k = 0; k < 2; ++k)
+            for (cudaEvent_t *e : {&in_ready[k], &in_free[k], &out_ready[k], &out_free[k]}) {
+                cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+                if (r != cudaSuccess) return r;
+            }
+        return cudaSuccess;
+    }
+    ~SlotEvents()
+    {
+        for (int k = 0; k < 2; ++k)
+            for (cudaEvent_t e : {in_ready[k], in_free[k], out_ready[k], out_free[k]})
+                if (e) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+extern "C" tm_status tm_Qtm_host(tm_ctx *ctx, const tm_gauge *U, int n, double *const *out_host,
+                                 const double *const *in_host, double kappa, double mu, int sign, void *stream)
+{
+    if (!ctx) return TM_ERR_ARG;
+    if (!U || n < 1 || !out_host || !in_host) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: bad arguments");
+    if (sign != 1 && sign != -1) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: sign must be +1 or -1");
+    std::set<const void *> ins;
+    for (int k = 0; k < n; ++k) {
+        if (!out_host[k] || !in_host[k]) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: null field pointer");
+        ins.insert(in_host[k]);
+    }
+    for (int k = 0; k < n; ++k)
+        if (ins.count(out_host[k])) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: an output buffer is also an input");
+
+    const unsigned vh = U->geom.vh;
+    const size_t cb = size_t(vh) * 24 * sizeof(double);  // canonical complex double [Vh][4][3]
+    const size_t cba = al256(cb), pba = al256(spinor_bytes(vh, U->prec));
+    tm_status st = grow_stage(ctx, 2 * (2 * cba + 2 * pba));
+    if (st != TM_OK) return st;
+    void *tmp = nullptr;  // tm_Qtm's scratch, grown now so that no call below reallocates it
+    st = tm_ctx_scratch(ctx, spinor_bytes(vh, U->prec), &tmp);
+    if (st != TM_OK) return st;
+    char *base = static_cast<char *>(ctx->stage);
+    double *can_in[2], *can_out[2];
+    void *p_in[2], *p_out[2];
+    for (int k = 0; k < 2; ++k) {
+        char *b = base + size_t(k) * (2 * cba + 2 * pba);
+        can_in[k] = reinterpret_cast<double *>(b);
+        can_out[k] = reinterpret_cast<double *>(b + cba);
+        p_in[k] = b + 2 * cba;
+        p_out[k] = b + 2 * cba + pba;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!ctx->copy_in) e = cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->copy_out) e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking);
+    SlotEvents ev;
+    if (e == cudaSuccess) e = ev.create();
+    if (e != cudaSuccess) return host_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_host: ") + cudaGetErrorString(e));
+
+    cudaStream_t s = (cudaStream_t)stream, ci = ctx->copy_in, co = ctx->copy_out;
+    st = TM_OK;
+    for (int k = 0; k < n && e == cudaSuccess && st == TM_OK; ++k) {
+        const int q = k & 1;
+        // copy in, once the pack of field k-2 has consumed this slot
+        e = cudaStreamWaitEvent(ci, ev.in_free[q], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(can_in[q], in_host[k], cb, cudaMemcpyHostToDevice, ci);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.in_ready[q], ci);
+        // pack, operator, and (once field k-2 has left this slot) unpack
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.in_ready[q], 0);
+        if (e == cudaSuccess) e = launch_pack_spinor(vh, U->prec, can_in[q], p_in[q], s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.in_free[q], s);
+        if (e == cudaSuccess) st = tm_Qtm(ctx, U, p_out[q], p_in[q], kappa, mu, sign, s);
+        if (e == cudaSuccess && st == TM_OK) e = cudaStreamWaitEvent(s, ev.out_free[q], 0);
+        if (e == cudaSuccess && st == TM_OK) e = launch_unpack_spinor(vh, U->prec, p_out[q], can_out[q], s);
+        if (e == cudaSuccess && st == TM_OK) e = cudaEventRecord(ev.out_ready[q], s);
+        // copy out
+        if (e == cudaSuccess && st == TM_OK) e = cudaStreamWaitEvent(co, ev.out_ready[q], 0);
+        if (e == cudaSuccess && st == TM_OK) e = cudaMemcpyAsync(out_host[k], can_out[q], cb, cudaMemcpyDeviceToHost, co);
+        if (e == cudaSuccess && st == TM_OK) e = cudaEventRecord(ev.out_free[q], co);
+    }
+    // drain every stream before the events go away, whatever happened
+    cudaError_t e1 = cudaStreamSynchronize(ci);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaError_t e3 = cudaStreamSynchronize(co);
+    if (st != TM_OK) return st;
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return host_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_host: ") + cudaGetErrorString(e));
+    return TM_OK;
+}

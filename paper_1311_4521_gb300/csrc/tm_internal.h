@@ -23,9 +23,18 @@ struct tm_ctx {
     size_t ws_bytes = 0;
     int autotune = 1;                // time launch configurations on first use
     std::map<std::string, std::pair<int, unsigned>> tuned;  // batched hop: key -> (pass width, CTA cap)
+    void *stage = nullptr;           // device staging slots of tm_Qtm_host (grow-only)
+    size_t stage_bytes = 0;
+    cudaStream_t copy_in = nullptr;  // copy streams of tm_Qtm_host (created on first use)
+    cudaStream_t copy_out = nullptr;
 };
 
 // Records trace event k of ctx on stream s, if tracing is on.
+// A device pointer that the kernels may read or write with 16-byte vector
+// accesses: non-null and 16-byte aligned (a misaligned vector access would
+// fault on the device, so the host rejects it first).
+inline bool bad_ptr(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
 inline void tm_trace_mark(tm_ctx *ctx, size_t k, cudaStream_t s)
 {
     if (k < ctx->trace.size()) cudaEventRecord(ctx->trace[k], s);
@@ -67,6 +76,8 @@ int link_nchunk(int prec, int recon);
 Coef coef_plain();
 Coef coef_qtm_a(double mut);
 Coef coef_qtm_b(double kappa, double mut);
+Coef coef_qtm_a_scaled(double kappa, double mut);
+Coef coef_qtm_b_unit(double mut);
 // gamma5 (1 + i mut gamma5) / (1 + mut^2): the odd field B of the force
 Coef coef_force_b(double mut);
 

@@ -40,6 +40,22 @@ Coef coef_qtm_b(double kappa, double mut)
     return Coef{-k2, 0, k2, 0, 1.0, mut, -1.0, mut};
 }
 
+// The same pair with -kappa^2 moved into the first launch: it writes
+// -kappa^2 M_oo^-1 H_oe x, and the second launch adds the hop of that with
+// the coefficients +1 (upper) and -1 (lower), a sign instead of a multiply.
+Coef coef_qtm_a_scaled(double kappa, double mut)
+{
+    double d = -kappa * kappa / (1.0 + mut * mut);
+    return Coef{d, -mut * d, d, mut * d, 0, 0, 0, 0};
+}
+
+Coef coef_qtm_b_unit(double mut)
+{
+    Coef c{1.0, 0, -1.0, 0, 1.0, mut, -1.0, mut};
+    c.unit = 1;
+    return c;
+}
+
 // ------------------------------------------------------------------ hop
 template <int P, int RECON, bool DAG, bool HASX>
 __global__ void __launch_bounds__(128, TM_HOP_MINB(P)) k_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,

@@ -73,7 +73,7 @@ extern "C" tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_
                                     double kappa, double mu, int sign, void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!U || !out_e_dev || !in_e_dev) return noalloc_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: null pointer");
+    if (!U || bad_ptr(out_e_dev) || bad_ptr(in_e_dev)) return noalloc_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: null or misaligned pointer");
     if (sign != 1 && sign != -1) return noalloc_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: sign must be +1 or -1");
     if (out_e_dev == in_e_dev) return noalloc_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: out and in must not overlap");
     size_t need = spinor_bytes(U->geom.vh, U->prec);
@@ -91,10 +91,10 @@ extern "C" tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_
     double mut = 2.0 * kappa * mu * sign;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, in_e_dev, tmp, nullptr,
-                               coef_qtm_a(mut), s, 128);
+                               coef_qtm_a_scaled(kappa, mut), s, 128);
     if (e == cudaSuccess)
         e = launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, tmp, out_e_dev, in_e_dev,
-                       coef_qtm_b(kappa, mut), s, 128);
+                       coef_qtm_b_unit(mut), s, 128);
     if (e != cudaSuccess)
         return noalloc_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_noalloc: launch: ") + cudaGetErrorString(e));
     return TM_OK;

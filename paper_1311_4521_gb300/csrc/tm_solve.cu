@@ -37,8 +37,8 @@ extern "C" tm_status tm_solve_eo(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
                                  void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!U_hi || !x_e || !x_o || !b_e || !b_o || !prm) {
-        ctx->err = "tm_solve_eo: null pointer";
+    if (!U_hi || bad_ptr(x_e) || bad_ptr(x_o) || bad_ptr(b_e) || bad_ptr(b_o) || !prm) {
+        ctx->err = "tm_solve_eo: null or misaligned pointer";
         return TM_ERR_ARG;
     }
     if (U_hi->prec != TM_F64) {
@@ -67,9 +67,9 @@ extern "C" tm_status tm_solve_eo(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
                        Coef{kappa, 0, -kappa, 0, 1, 0, -1, 0}, s, 128);
     // src = Q(-mu) c_e = Q^dag gamma5 bhat_e
     if (e == cudaSuccess)
-        e = launch_hop(g, F64, U_hi->recon, false, TM_OE, U_hi->links, c_e, t_o, nullptr, coef_qtm_a(-mut), s, 128);
+        e = launch_hop(g, F64, U_hi->recon, false, TM_OE, U_hi->links, c_e, t_o, nullptr, coef_qtm_a_scaled(kappa, -mut), s, 128);
     if (e == cudaSuccess)
-        e = launch_hop(g, F64, U_hi->recon, false, TM_EO, U_hi->links, t_o, src, c_e, coef_qtm_b(kappa, -mut), s, 128);
+        e = launch_hop(g, F64, U_hi->recon, false, TM_EO, U_hi->links, t_o, src, c_e, coef_qtm_b_unit(-mut), s, 128);
     if (e != cudaSuccess) {
         ctx->err = std::string("tm_solve_eo: source: ") + cudaGetErrorString(e);
         return TM_ERR_CUDA;

@@ -77,6 +77,7 @@ def _load() -> ctypes.CDLL:
         "tm_force_ex": ([P, P, P, P, D, D, I, I, P], I),
         "tm_solve_eo": ([P, P, P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
         "tm_Qtm_batch": ([P, I, P, P, P, D, D, I, P], I),
+        "tm_Qtm_host": ([P, P, I, P, P, D, D, I, P], I),
         "tm_cg_QdagQ_batch": ([P, I, P, P, P, P, ctypes.POINTER(CgParams), P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -223,6 +224,16 @@ def tm_Qtm_batch(ctx, gauges, outs, ins, kappa, mu, sign=1, stream=None):
                                  _stream(stream)))
 
 
+def tm_Qtm_host(ctx, U, outs_host, ins_host, kappa, mu, sign=1, stream=None):
+    """Q_tm on host-resident fields: outs_host[k] = Q ins_host[k] (host buffers of complex double
+    [Vh][4][3]; pinned for overlapped copies).  Synchronous."""
+    n = len(ins_host)
+    if len(outs_host) != n:
+        raise ValueError("tm_Qtm_host: as many outputs as inputs")
+    _check(ctx, lib.tm_Qtm_host(ctx, U, n, _parr(outs_host), _parr(ins_host), float(kappa), float(mu), int(sign),
+                                _stream(stream)))
+
+
 def tm_cg_QdagQ_batch(ctx, U_hi, U_lo, xs, bs, params: CgParams, stream=None):
     """Returns (status, [CgInfo per system]); raises only for argument and CUDA errors."""
     n = len(U_hi)
@@ -347,6 +358,15 @@ class Context:
         F = torch.empty((4, V, 3, 3, 2), dtype=torch.float64, device=self.device)
         tm_force_ex(self.handle, U.handle, F, X_e, kappa, mu, mode, scheme)
         return torch.view_as_complex(F)
+
+    def Qtm_host(self, U: Gauge, outs, ins, kappa, mu, sign=1):
+        """Q_tm on host tensors (complex128 [Vh, 4, 3], contiguous, on the CPU; pin them for overlap)."""
+        for t in list(outs) + list(ins):
+            if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == torch.complex128
+                    and t.is_contiguous() and t.numel() == 12 * U.vh):
+                raise ValueError("Qtm_host: fields must be contiguous complex128 CPU tensors of Vh x 4 x 3")
+        tm_Qtm_host(self.handle, U.handle, outs, ins, kappa, mu, sign)
+        return outs
 
     def Qtm_batch(self, gauges, outs, ins, kappa, mu, sign=1):
         tm_Qtm_batch(self.handle, [g.handle for g in gauges], outs, ins, kappa, mu, sign)

@@ -126,6 +126,11 @@ def test_argument_errors(ctx):
     assert e.value.status == tmhop.TM_ERR_ARG
     with pytest.raises(tmhop.TmError):
         ctx.hopping_eo(g, buf, ctx.empty(8, "f64"), 5)
+    # a field pointer 8 bytes off a 16-byte boundary is rejected before any launch
+    flat = ctx.empty(9, "f64")
+    with pytest.raises(tmhop.TmError) as e:
+        ctx.Qtm(g, flat[8:], buf, 0.1, 0.1)
+    assert e.value.status == tmhop.TM_ERR_ARG
 
 
 # 32^3x64, near-thermalised links exp(0.3 i A), kappa = 0.1394, mu = 0.0015:
