@@ -446,7 +446,7 @@ def cg_section(args, ctx, tmhop, torch, F, allmax, barrier, keep_host=False):
     bx = ctx.pack(b, "f64x")
     x = ctx.empty(vh, "f64")
     out = {"lattice": list(dims), "tol": 1e-10, "kappa": KAPPA, "mu": MU, "reliable_every": 50,
-           "reliable_delta": args.cg_delta, "source": "Gaussian, seed 2013", "time": "CUDA events around one warm solve"}
+           "reliable_delta": args.cg_delta if args.cg_delta >= 0 else {"f32": 1e-3, "f16": 2 ** -5.5}, "source": "Gaussian, seed 2013", "time": "CUDA events around one warm solve"}
     stream = torch.cuda.current_stream()
     runs = (("fp64", gh, bd, None), ("mixed_f32", gh, bd, lo["mixed_f32"]), ("mixed_f16", gh, bd, lo["mixed_f16"]),
             ("fp64x", gx, bx, None), ("mixed_f32_fp64x", gx, bx, lo["mixed_f32"]),
@@ -744,8 +744,9 @@ def main() -> None:
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--only", choices=["batch-qtm", "cg", "force", "solve"], default=None,
                     help="run one section alone (for profiling captures)")
-    ap.add_argument("--cg-delta", type=float, default=0.1,
-                    help="reliable-update threshold of the mixed-precision solvers (residual drop factor)")
+    ap.add_argument("--cg-delta", type=float, default=-1.0,
+                    help="reliable-update threshold of the mixed-precision solvers (residual drop factor); "
+                         "negative: the library's automatic choice (FP32 1e-3, FP16 0.022)")
     ap.add_argument("--force-scheme", choices=["owner", "atomic", "halo"], default="owner",
                     help="force assembly for --only force")
     ap.add_argument("--cg-lattice", type=lambda v: tuple(int(a) for a in v.split(",")), default=(48, 48, 48, 96))

@@ -158,7 +158,9 @@ typedef struct {
     double reliable_delta; /* reduced-precision inner solver: FP64 reliable update (x += y,
                               r = b - Q^dag Q x in FP64) as soon as the recursive |r| has fallen
                               below reliable_delta times its largest value since the previous
-                              one (0 <= delta < 1; 0: only every reliable_every iterations) */
+                              one (delta < 1; 0: only every reliable_every iterations; negative:
+                              automatic, sqrt of the inner format's unit roundoff and at least
+                              1e-3, i.e. 1e-3 for TM_F32 and 0.022 for TM_F16) */
 } tm_cg_params;
 
 /* Results of tm_cg_QdagQ. */

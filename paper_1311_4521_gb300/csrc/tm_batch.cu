@@ -490,8 +490,7 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
     auto t_start = std::chrono::steady_clock::now();
     if (!ctx) return TM_ERR_ARG;
     if (nsys < 1 || !U_hi || !x_dev || !b_dev || !prm) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad arguments");
-    if (!(prm->tol > 0.0) || prm->maxiter < 0 || prm->reliable_every < 1 || !(prm->reliable_delta >= 0.0) ||
-        !(prm->reliable_delta < 1.0))
+    if (!(prm->tol > 0.0) || prm->maxiter < 0 || prm->reliable_every < 1 || !(prm->reliable_delta < 1.0))
         return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad solver parameters");
     std::vector<const tm_gauge *> handles;
     std::vector<std::vector<int>> members;
@@ -590,7 +589,8 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
         h = CgScalars{};
         h.tol2 = prm->tol * prm->tol;
         h.maxiter = prm->maxiter;
-        h.delta2 = prm->reliable_delta * prm->reliable_delta;
+        const double d = reliable_delta_for(prm->reliable_delta, B.P);
+        h.delta2 = d * d;
         h.every = prm->reliable_every;
         h.mixed = 1;
     }

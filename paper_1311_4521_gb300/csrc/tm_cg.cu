@@ -454,10 +454,9 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     if (!U_lo) U_lo = U_hi;
     if (memcmp(U_lo->dims, U_hi->dims, sizeof U_hi->dims) || memcmp(U_lo->bc, U_hi->bc, sizeof U_hi->bc))
         return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi and U_lo describe different lattices");
-    if (!(prm->tol > 0.0) || prm->maxiter < 0 || prm->reliable_every < 1 || !(prm->reliable_delta >= 0.0) ||
-        !(prm->reliable_delta < 1.0))
+    if (!(prm->tol > 0.0) || prm->maxiter < 0 || prm->reliable_every < 1 || !(prm->reliable_delta < 1.0))
         return cg_fail(ctx, TM_ERR_ARG,
-                       "tm_cg_QdagQ: need tol > 0, maxiter >= 0, reliable_every >= 1, 0 <= reliable_delta < 1");
+                       "tm_cg_QdagQ: need tol > 0, maxiter >= 0, reliable_every >= 1, reliable_delta < 1");
     if (x_dev == b_dev) return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: x and b must not overlap");
 
     Solver S;
@@ -503,7 +502,10 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     CgScalars h{};
     h.tol2 = prm->tol * prm->tol;
     h.maxiter = prm->maxiter;
-    h.delta2 = prm->reliable_delta * prm->reliable_delta;
+    {
+        const double d = w.mixed ? reliable_delta_for(prm->reliable_delta, w.P) : 0.0;
+        h.delta2 = d * d;
+    }
     h.every = prm->reliable_every;
     h.mixed = w.mixed ? 1 : 0;
     cudaError_t e = cudaMemcpyAsync(w.s, &h, sizeof h, cudaMemcpyHostToDevice, s);

@@ -40,6 +40,20 @@ inline void tm_trace_mark(tm_ctx *ctx, size_t k, cudaStream_t s)
     if (k < ctx->trace.size()) cudaEventRecord(ctx->trace[k], s);
 }
 
+// The reliable-update threshold of a mixed-precision solve: the caller's
+// value, or for a negative one the square root of the unit roundoff of the
+// inner storage format, at least 1e-3 (FP32 1e-3, FP16 0.022).  Measured on
+// 32^3x64: FP32 inner solves need no more iterations down to 1e-3 and take
+// the fewest reliable updates there; FP16 ones start to need more
+// iterations below about 0.01.
+inline double reliable_delta_for(double delta, int inner_prec)
+{
+    if (delta >= 0.0) return delta;
+    const double u = inner_prec == TM_F16 ? 0x1p-11 : 0x1p-24;
+    const double d = __builtin_sqrt(u);
+    return d > 1e-3 ? d : 1e-3;
+}
+
 // Grows the context's scratch buffer to at least `bytes` and returns it.
 tm_status tm_ctx_scratch(tm_ctx *ctx, size_t bytes, void **ptr);
 // Grows the context's solver workspace to at least `bytes` and returns it.

@@ -345,7 +345,7 @@ class Context:
         return out
 
     def solve_eo(self, U_hi: Gauge, x_e, x_o, b_e, b_o, kappa, mu, tol=1e-10, maxiter=30000,
-                 U_lo: Gauge | None = None, reliable_every=50, use_graph=True, reliable_delta=0.1):
+                 U_lo: Gauge | None = None, reliable_every=50, use_graph=True, reliable_delta=-1.0):
         prm = CgParams(float(kappa), float(mu), float(tol), int(maxiter), int(reliable_every), int(bool(use_graph)),
                        float(reliable_delta))
         st, info = tm_solve_eo(self.handle, U_hi.handle, U_lo.handle if U_lo is not None else None,
@@ -373,7 +373,7 @@ class Context:
         return outs
 
     def cg_batch(self, U_hi, xs, bs, kappa, mu, tol=1e-10, maxiter=30000, U_lo=None, reliable_every=50,
-                 use_graph=True, reliable_delta=0.1):
+                 use_graph=True, reliable_delta=-1.0):
         """Solves Q^dag Q x[k] = b[k] for all k at once.  Returns (status, [info dict per system])."""
         prm = CgParams(float(kappa), float(mu), float(tol), int(maxiter), int(reliable_every), int(bool(use_graph)),
                        float(reliable_delta))
@@ -382,7 +382,7 @@ class Context:
         return st, [i.as_dict() for i in infos]
 
     def cg(self, U_hi: Gauge, x, b, kappa, mu, tol=1e-10, maxiter=30000, U_lo: Gauge | None = None,
-           reliable_every=50, use_graph=True, reliable_delta=0.1):
+           reliable_every=50, use_graph=True, reliable_delta=-1.0):
         """Solves Q^dag Q x = b (x: packed FP64 even field, in/out).  Returns (status, info dict)."""
         prm = CgParams(float(kappa), float(mu), float(tol), int(maxiter), int(reliable_every), int(bool(use_graph)),
                        float(reliable_delta))
