@@ -275,10 +275,8 @@ cudaError_t hop_launch(const tm_gauge *U, int parity, const void *in, void *out,
     using V = typename LinkIO<P, RECON>::V;
     const V *l = static_cast<const V *>(U->links);
     unsigned grid = blocks(U->geom.vh, HOP_BLOCK);
-    if (norm)
-        k_cg_hop<P, RECON, true><<<grid, HOP_BLOCK, 0, st>>>(U->geom, parity, l, in, out, x, k, w.partials, w.s, gate);
-    else
-        k_cg_hop<P, RECON, false><<<grid, HOP_BLOCK, 0, st>>>(U->geom, parity, l, in, out, x, k, w.partials, w.s, gate);
+    auto kern = norm ? k_cg_hop<P, RECON, true> : k_cg_hop<P, RECON, false>;
+    kern<<<grid, HOP_BLOCK, 0, st>>>(U->geom, parity, l, in, out, x, k, w.partials, w.s, gate);
     return cudaGetLastError();
 }
 

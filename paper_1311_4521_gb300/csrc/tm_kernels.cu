@@ -84,13 +84,9 @@ static cudaError_t hop_dispatch(const Geom &g, bool dag, int p, const void *link
     using V = typename LinkIO<P, RECON>::V;
     const V *l = static_cast<const V *>(links);
     unsigned grid = (g.vh + block - 1) / block;
-    if (dag) {
-        if (x) k_hop<P, RECON, true, true><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
-        else k_hop<P, RECON, true, false><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
-    } else {
-        if (x) k_hop<P, RECON, false, true><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
-        else k_hop<P, RECON, false, false><<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
-    }
+    auto kern = dag ? (x ? k_hop<P, RECON, true, true> : k_hop<P, RECON, true, false>)
+                    : (x ? k_hop<P, RECON, false, true> : k_hop<P, RECON, false, false>);
+    kern<<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
     return cudaGetLastError();
 }
 
