@@ -149,3 +149,33 @@ def test_Qtm_production_size(ctx, prod, prec, recon):
     dims, U, psi, want = prod
     got = gpu_apply(ctx, dims, U, psi, prec, recon, "qtm", kappa=0.1394, mu=0.0015)
     assert rel(got, want) < TOL[prec]
+
+
+# degenerate parameters of the method: kappa = 0 (Q = gamma5 (1 + i mut gamma5)
+# acting alone), mu = 0 (plain Wilson), both, the free field (U = 1), an
+# all-zero input, and all-periodic boundaries
+@pytest.mark.parametrize("kappa,mu", [(0.0, 0.01), (0.16, 0.0), (0.0, 0.0)])
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64x", 12), ("f32", 12), ("f16", 12)])
+def test_Qtm_degenerate_parameters(ctx, small, kappa, mu, prec, recon):
+    dims, U, psi = small
+    want = O.Qtm(dims, U, psi, kappa, mu)
+    got = gpu_apply(ctx, dims, U, psi, prec, recon, "qtm", kappa=kappa, mu=mu)
+    assert rel(got, want) < TOL[prec]
+    if kappa == 0.0 and mu == 0.0:   # Q = gamma5: exact in every storage format up to its rounding
+        g5 = psi.copy()
+        g5[:, 2:] *= -1
+        assert rel(got, g5) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 12), ("f16", 12)])
+def test_free_field_zero_input_periodic(ctx, prec, recon):
+    dims = (4, 6, 4, 8)
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, 0, "unit")
+    psi = F.gaussian_spinor(vh, 9, 4)
+    for bc in ((1, 1, 1, 1), (-1, 1, 1, 1)):
+        want = O.Qtm(dims, U, psi, 0.125, 0.05, bc=bc)
+        assert rel(gpu_apply(ctx, dims, U, psi, prec, recon, "qtm", kappa=0.125, mu=0.05, bc=bc), want) < TOL[prec]
+    zero = np.zeros_like(psi)
+    out = gpu_apply(ctx, dims, U, zero, prec, recon, "qtm", kappa=0.125, mu=0.05)
+    assert np.all(out == 0)
