@@ -92,6 +92,13 @@ tm_status tm_ctx_trace(tm_ctx *ctx, void *const *events, int nevents);
  * context's lifetime; off, a fixed configuration is used. */
 tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on);
 
+/* Text report of the launch configurations the context has chosen so far,
+ * one line per batch shape: "<key> nrb=<pass width> cap=<CTA cap> ms3=<time
+ * of three launches at selection>".  Writes at most size bytes including the
+ * terminating NUL (truncating) and returns the size the full report needs;
+ * buf may be NULL to ask for that size. */
+size_t tm_ctx_tune_report(const tm_ctx *ctx, char *buf, size_t size);
+
 /* ---- fields --------------------------------------------------------------- */
 
 /* Bytes of one packed one-parity spinor field of Vh sites in precision prec:

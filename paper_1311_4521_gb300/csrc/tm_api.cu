@@ -101,6 +101,25 @@ tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on)
     return TM_OK;
 }
 
+size_t tm_ctx_tune_report(const tm_ctx *ctx, char *buf, size_t size)
+{
+    if (!ctx) return 0;
+    std::string rep;
+    for (const auto &kv : ctx->tuned) {
+        char line[256];
+        auto ms = ctx->tuned_ms.find(kv.first);
+        snprintf(line, sizeof line, "%s nrb=%d cap=%u ms3=%.4f\n", kv.first.c_str(), kv.second.first,
+                 kv.second.second, ms == ctx->tuned_ms.end() ? 0.0 : double(ms->second));
+        rep += line;
+    }
+    if (buf && size > 0) {
+        const size_t n = rep.size() < size - 1 ? rep.size() : size - 1;
+        memcpy(buf, rep.data(), n);
+        buf[n] = '\0';
+    }
+    return rep.size() + 1;
+}
+
 tm_status tm_ctx_trace(tm_ctx *ctx, void *const *events, int nevents)
 {
     if (!ctx) return TM_ERR_ARG;

@@ -306,22 +306,27 @@ cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_
 
 // Times a candidate hop table with a (parity 1, rin -> rout) launch; returns ms.
 // rin and rout must be fields of the table's precision.
+// Time of three hop launches with table t: the median of three rounds, so
+// that one disturbed round (clock ramp, another process's work) can neither
+// hide a slow configuration nor discard a fast one.
 float time_table(int prec, int recon, const HopTable &t, const BSys *sys, int rin, int rout, cudaStream_t st)
 {
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
+    cudaEvent_t ev[4];
+    for (auto &e : ev) cudaEventCreate(&e);
     Coef k = coef_plain();
     bhop(prec, recon, t, sys, 1, rin, rout, -1, k, false, 0, st);
-    cudaEventRecord(a, st);
-    for (int r = 0; r < 3; ++r) bhop(prec, recon, t, sys, 1, rin, rout, -1, k, false, 0, st);
-    cudaEventRecord(b, st);
-    cudaEventSynchronize(b);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, a, b);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+    float ms[3] = {0.f, 0.f, 0.f};
+    cudaEventRecord(ev[0], st);
+    for (int round = 0; round < 3; ++round) {
+        for (int r = 0; r < 3; ++r) bhop(prec, recon, t, sys, 1, rin, rout, -1, k, false, 0, st);
+        cudaEventRecord(ev[round + 1], st);
+    }
+    cudaEventSynchronize(ev[3]);
+    for (int round = 0; round < 3; ++round) cudaEventElapsedTime(&ms[round], ev[round], ev[round + 1]);
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (cudaGetLastError() != cudaSuccess) return 1e30f;
+    std::sort(ms, ms + 3);
+    return ms[1];
 }
 
 }  // namespace
@@ -369,6 +374,7 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
         }
     }
     ctx->tuned[key] = {best_nrb, best_cap};
+    ctx->tuned_ms[key] = best;
     cudaError_t e = build_table(tmpl, best_nrb, best_cap, out, dev, st, host);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;

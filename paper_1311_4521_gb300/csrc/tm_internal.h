@@ -23,6 +23,7 @@ struct tm_ctx {
     size_t ws_bytes = 0;
     int autotune = 1;                // time launch configurations on first use
     std::map<std::string, std::pair<int, unsigned>> tuned;  // batched hop: key -> (pass width, CTA cap)
+    std::map<std::string, float> tuned_ms;                  // and the winner's time for 3 launches
     void *stage = nullptr;           // device staging slots of tm_Qtm_host (grow-only)
     size_t stage_bytes = 0;
     cudaStream_t copy_in = nullptr;  // copy streams of tm_Qtm_host (created on first use)

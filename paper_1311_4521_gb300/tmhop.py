@@ -73,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "tm_Qtm_noalloc": ([P, P, P, P, D, D, I, P], I),
         "tm_cg_QdagQ": ([P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
         "tm_ctx_set_autotune": ([P, I], I),
+        "tm_ctx_tune_report": ([P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_size_t),
         "tm_force": ([P, P, P, P, D, D, I, P], I),
         "tm_force_ex": ([P, P, P, P, D, D, I, I, P], I),
         "tm_solve_eo": ([P, P, P, P, P, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), P], I),
@@ -210,6 +211,14 @@ def tm_force_ex(ctx, U, F_dev, X_e_dev, kappa, mu, mode=TM_FORCE_SU3, scheme=TM_
 
 def tm_ctx_set_autotune(ctx, on: bool) -> None:
     _check(ctx, lib.tm_ctx_set_autotune(ctx, int(bool(on))))
+
+
+def tm_ctx_tune_report(ctx) -> str:
+    """The launch configurations the context's autotuner has chosen, one line per batch shape."""
+    n = lib.tm_ctx_tune_report(ctx, None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib.tm_ctx_tune_report(ctx, buf, n)
+    return buf.value.decode()
 
 
 def _parr(items):

@@ -61,6 +61,10 @@ def test_Qtm_batch_matches_oracle(ctx, prec, spec, autotune):
             assert rel(ctx.unpack(out, psi.shape[0], prec).cpu().numpy(), want) < TOL[prec]
     for g in gauges:
         g.close()
+    if autotune:   # the autotuner's choice for this shape is on the context's report
+        rep = tmhop.tm_ctx_tune_report(ctx.handle)
+        key = "bhop/%d/%d/" % (tmhop.PREC[prec], RECON[prec])
+        assert any(line.startswith(key) and " nrb=" in line and " ms3=" in line for line in rep.splitlines()), rep
     tmhop.tm_ctx_set_autotune(ctx.handle, True)
 
 
