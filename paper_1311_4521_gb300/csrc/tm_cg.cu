@@ -6,7 +6,8 @@
 // management the paper measures as overhead (Sec. 3).  Here every scalar of
 // the iteration lives in device memory: each reduction is fused into the
 // kernel that produces its operand (<p, Q^dag Q p> = |Q p|^2 in the launch
-// that writes Q p, |r|^2 in the vector update), finished by the last block
+// that writes Q p; the vector update and |r|^2 in the launch that computes
+// Q^dag Q p, which is therefore never stored), finished by the last block
 // to arrive in a fixed order (bit-reproducible, no atomics on the values),
 // and alpha, beta and the stopping test are computed there too.  The host
 // only synchronises once per segment of `reliable_every` iterations; the
@@ -71,14 +72,23 @@ __device__ void reduce_finish(double v, double *partials, CgScalars *s, int op)
 constexpr int HOP_BLOCK = 128;
 constexpr int LA_BLOCK = 256;
 
-// Hop with the twisted-mass epilogue; NORM also reduces |out|^2 into pAp.
-template <int P, int RECON, bool NORM>
+// Hop with the twisted-mass epilogue.  MODE HOP_NORM also reduces |out|^2
+// into pAp; MODE HOP_UPDATE is the last hop of Q^dag Q p: instead of storing
+// its result Ap it applies the CG update at once, y += alpha p and
+// r -= alpha Ap (y in precision PY), and reduces |r|^2 into rr_new, so Ap is
+// never written to memory and read back.
+enum { HOP_PLAIN = 0, HOP_NORM = 1, HOP_UPDATE = 2 };
+
+template <int P, int RECON, int MODE>
 __global__ void __launch_bounds__(HOP_BLOCK, TM_HOP_MINB(P)) k_cg_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,
                                                       const void *__restrict__ in, void *__restrict__ out,
-                                                      const void *__restrict__ x, Coef k, double *partials,
-                                                      CgScalars *s, int gate)
+                                                      const void *__restrict__ x, Coef k, void *__restrict__ y,
+                                                      void *__restrict__ r, const void *__restrict__ pdir,
+                                                      double *partials, CgScalars *s, int gate)
 {
     using R = typename SpinorIO<P>::R;
+    constexpr int PY = P == F16 ? F32 : P;
+    using RY = typename SpinorIO<PY>::R;
     if (gated(s, gate)) return;
     unsigned i = blockIdx.x * HOP_BLOCK + threadIdx.x;
     double nrm = 0.0;
@@ -92,46 +102,33 @@ __global__ void __launch_bounds__(HOP_BLOCK, TM_HOP_MINB(P)) k_cg_hop(Geom g, in
         } else {
             epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
         }
-        SpinorIO<P>::store(out, g.vh, i, o);
-        if (NORM) nrm = norm2(o);
-    }
-    if (NORM) reduce_finish<HOP_BLOCK>(nrm, partials, s, FIN_PAP);
-}
-
-// y += alpha p, r -= alpha Ap, rr_new = |r|^2 (y in precision PY).
-template <int P, int PY>
-__global__ void __launch_bounds__(LA_BLOCK, (P == F64 || P == F64X) ? 3 : 4) k_cg_update(unsigned vh, void *y, void *r, const void *p, const void *Ap,
-                                                        double *partials, CgScalars *s)
-{
-    using R = typename SpinorIO<P>::R;
-    using RY = typename SpinorIO<PY>::R;
-    if (s->done) return;
-    unsigned i = blockIdx.x * LA_BLOCK + threadIdx.x;
-    double nrm = 0.0;
-    if (i < vh) {
-        const double alpha = s->alpha;
-        Spinor<R> pv, av, rv;
-        Spinor<RY> yv;
-        SpinorIO<P>::load(p, vh, i, pv);
-        SpinorIO<P>::load(Ap, vh, i, av);
-        SpinorIO<P>::load(r, vh, i, rv);
-        SpinorIO<PY>::load(y, vh, i, yv);
-        const R a = to_R<R>(alpha);
-        const RY ay = to_R<RY>(alpha);
+        if (MODE == HOP_UPDATE) {
+            const double alpha = s->alpha;
+            Spinor<R> pv, rv;
+            Spinor<RY> yv;
+            SpinorIO<P>::load(pdir, g.vh, i, pv);
+            SpinorIO<P>::load(r, g.vh, i, rv);
+            SpinorIO<PY>::load(y, g.vh, i, yv);
+            const R a = to_R<R>(alpha);
+            const RY ay = to_R<RY>(alpha);
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp)
+            for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                yv[sp][c].re += ay * RY(pv[sp][c].re);
-                yv[sp][c].im += ay * RY(pv[sp][c].im);
-                rv[sp][c].re -= a * av[sp][c].re;
-                rv[sp][c].im -= a * av[sp][c].im;
-            }
-        SpinorIO<PY>::store(y, vh, i, yv);
-        SpinorIO<P>::store(r, vh, i, rv);
-        nrm = norm2(rv);
+                for (int c = 0; c < 3; ++c) {
+                    yv[sp][c].re += ay * RY(pv[sp][c].re);
+                    yv[sp][c].im += ay * RY(pv[sp][c].im);
+                    rv[sp][c].re -= a * o[sp][c].re;
+                    rv[sp][c].im -= a * o[sp][c].im;
+                }
+            SpinorIO<PY>::store(y, g.vh, i, yv);
+            SpinorIO<P>::store(r, g.vh, i, rv);
+            nrm = norm2(rv);
+        } else {
+            SpinorIO<P>::store(out, g.vh, i, o);
+            if (MODE == HOP_NORM) nrm = norm2(o);
+        }
     }
-    reduce_finish<LA_BLOCK>(nrm, partials, s, FIN_RR_UPDATE);
+    if (MODE != HOP_PLAIN) reduce_finish<HOP_BLOCK>(nrm, partials, s, MODE == HOP_NORM ? FIN_PAP : FIN_RR_UPDATE);
 }
 
 // p = r + beta p with beta = rr_new / rr (restart: p = r); then rr = rr_new.
@@ -261,7 +258,7 @@ struct Work {
     // FP64 fields
     void *x, *b, *ax, *t_hi, *q_hi, *r_hi;
     // inner fields (precision P), y in PY
-    void *r, *p, *Ap, *q, *t, *y;
+    void *r, *p, *q, *t, *y;
     double *partials;
     CgScalars *s;
 };
@@ -269,57 +266,46 @@ struct Work {
 unsigned blocks(unsigned vh, int b) { return (vh + b - 1) / b; }
 
 template <int P, int RECON>
-cudaError_t hop_launch(const tm_gauge *U, int parity, const void *in, void *out, const void *x, const Coef &k, bool norm,
+cudaError_t hop_launch(const tm_gauge *U, int parity, const void *in, void *out, const void *x, const Coef &k, int mode,
                        const Work &w, int gate, cudaStream_t st)
 {
     using V = typename LinkIO<P, RECON>::V;
     const V *l = static_cast<const V *>(U->links);
     unsigned grid = blocks(U->geom.vh, HOP_BLOCK);
-    auto kern = norm ? k_cg_hop<P, RECON, true> : k_cg_hop<P, RECON, false>;
-    kern<<<grid, HOP_BLOCK, 0, st>>>(U->geom, parity, l, in, out, x, k, w.partials, w.s, gate);
+    auto kern = mode == HOP_UPDATE ? k_cg_hop<P, RECON, HOP_UPDATE>
+                                   : mode == HOP_NORM ? k_cg_hop<P, RECON, HOP_NORM> : k_cg_hop<P, RECON, HOP_PLAIN>;
+    kern<<<grid, HOP_BLOCK, 0, st>>>(U->geom, parity, l, in, out, x, k, w.y, w.r, w.p, w.partials, w.s, gate);
     return cudaGetLastError();
 }
 
-cudaError_t hop(const tm_gauge *U, int parity, const void *in, void *out, const void *x, const Coef &k, bool norm,
+cudaError_t hop(const tm_gauge *U, int parity, const void *in, void *out, const void *x, const Coef &k, int mode,
                 const Work &w, int gate, cudaStream_t st)
 {
     switch (U->prec * 100 + U->recon) {
-    case F64 * 100 + 18: return hop_launch<F64, 18>(U, parity, in, out, x, k, norm, w, gate, st);
-    case F64 * 100 + 12: return hop_launch<F64, 12>(U, parity, in, out, x, k, norm, w, gate, st);
-    case F32 * 100 + 18: return hop_launch<F32, 18>(U, parity, in, out, x, k, norm, w, gate, st);
-    case F32 * 100 + 12: return hop_launch<F32, 12>(U, parity, in, out, x, k, norm, w, gate, st);
-    case F16 * 100 + 12: return hop_launch<F16, 12>(U, parity, in, out, x, k, norm, w, gate, st);
-    case F64X * 100 + 18: return hop_launch<F64X, 18>(U, parity, in, out, x, k, norm, w, gate, st);
-    case F64X * 100 + 12: return hop_launch<F64X, 12>(U, parity, in, out, x, k, norm, w, gate, st);
+    case F64 * 100 + 18: return hop_launch<F64, 18>(U, parity, in, out, x, k, mode, w, gate, st);
+    case F64 * 100 + 12: return hop_launch<F64, 12>(U, parity, in, out, x, k, mode, w, gate, st);
+    case F32 * 100 + 18: return hop_launch<F32, 18>(U, parity, in, out, x, k, mode, w, gate, st);
+    case F32 * 100 + 12: return hop_launch<F32, 12>(U, parity, in, out, x, k, mode, w, gate, st);
+    case F16 * 100 + 12: return hop_launch<F16, 12>(U, parity, in, out, x, k, mode, w, gate, st);
+    case F64X * 100 + 18: return hop_launch<F64X, 18>(U, parity, in, out, x, k, mode, w, gate, st);
+    case F64X * 100 + 12: return hop_launch<F64X, 12>(U, parity, in, out, x, k, mode, w, gate, st);
     }
     return cudaErrorInvalidValue;
 }
 
-// out = Q(-mu) Q(mu) in with temporaries t (odd) and q (even); norm: |Q in|^2 -> pAp.
-cudaError_t qdagq(const tm_gauge *U, double kappa, double mu, const void *in, void *out, void *t, void *q, bool norm,
-                  const Work &w, int gate, cudaStream_t st)
+// out = Q(-mu) Q(mu) in with temporaries t (odd) and q (even).  With
+// `iterate` (the CG iteration, in = p): the second launch also reduces
+// |Q p|^2 into pAp and alpha, and the last one applies the CG update instead
+// of writing out (which may then be null).
+cudaError_t qdagq(const tm_gauge *U, double kappa, double mu, const void *in, void *out, void *t, void *q,
+                  bool iterate, const Work &w, int gate, cudaStream_t st)
 {
     double mut = 2.0 * kappa * mu;
-    cudaError_t e = hop(U, 1, in, t, nullptr, coef_qtm_a_scaled(kappa, mut), false, w, gate, st);
-    if (e == cudaSuccess) e = hop(U, 0, t, q, in, coef_qtm_b_unit(mut), norm, w, gate, st);
-    if (e == cudaSuccess) e = hop(U, 1, q, t, nullptr, coef_qtm_a_scaled(kappa, -mut), false, w, gate, st);
-    if (e == cudaSuccess) e = hop(U, 0, t, out, q, coef_qtm_b_unit(-mut), false, w, gate, st);
+    cudaError_t e = hop(U, 1, in, t, nullptr, coef_qtm_a_scaled(kappa, mut), HOP_PLAIN, w, gate, st);
+    if (e == cudaSuccess) e = hop(U, 0, t, q, in, coef_qtm_b_unit(mut), iterate ? HOP_NORM : HOP_PLAIN, w, gate, st);
+    if (e == cudaSuccess) e = hop(U, 1, q, t, nullptr, coef_qtm_a_scaled(kappa, -mut), HOP_PLAIN, w, gate, st);
+    if (e == cudaSuccess) e = hop(U, 0, t, out, q, coef_qtm_b_unit(-mut), iterate ? HOP_UPDATE : HOP_PLAIN, w, gate, st);
     return e;
-}
-
-template <int P, int PY>
-cudaError_t update(const Work &w, cudaStream_t st)
-{
-    k_cg_update<P, PY><<<blocks(w.vh, LA_BLOCK), LA_BLOCK, 0, st>>>(w.vh, w.y, w.r, w.p, w.Ap, w.partials, w.s);
-    return cudaGetLastError();
-}
-
-cudaError_t update_any(const Work &w, cudaStream_t st)
-{
-    if (w.P == F64) return update<F64, F64>(w, st);
-    if (w.P == F64X) return update<F64X, F64X>(w, st);
-    if (w.P == F32) return update<F32, F32>(w, st);
-    return update<F16, F32>(w, st);
 }
 
 cudaError_t pupdate(const Work &w, int skip, int restart, cudaStream_t st)
@@ -380,8 +366,7 @@ struct Solver {
     // reliable-update kernels, gated on the device flag the update sets.
     cudaError_t iteration(cudaStream_t st) const
     {
-        cudaError_t e = qdagq(Ul, kappa, mu, w.p, w.Ap, w.t, w.q, true, w, 1, st);
-        if (e == cudaSuccess) e = update_any(w, st);
+        cudaError_t e = qdagq(Ul, kappa, mu, w.p, nullptr, w.t, w.q, true, w, 1, st);
         if (e == cudaSuccess && w.mixed) {
             e = accum(w, 2, st);
             if (e == cudaSuccess) e = qdagq(Uh, kappa, mu, w.x, w.ax, w.t_hi, w.q_hi, false, w, 2, st);
@@ -470,11 +455,11 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     w.PY = w.P == F16 ? F32 : w.P;
     if (!w.mixed) S.Ul = U_hi;
 
-    // workspace: FP64 ax, t_hi, q_hi (+ r in plain mode), inner r, p, Ap, q, t, y, partials, scalars
+    // workspace: FP64 ax, t_hi, q_hi (+ r in plain mode), inner r, p, q, t, y, partials, scalars
     const size_t f64 = spinor_bytes(w.vh, w.PH), flo = spinor_bytes(w.vh, w.P), fy = spinor_bytes(w.vh, w.PY);
     auto al = [](size_t n) { return (n + 255) & ~size_t(255); };
     const size_t nblk = blocks(w.vh, 128) + 1;
-    size_t need = 3 * al(f64) + 5 * al(flo) + (w.mixed ? al(fy) : 0) + al(nblk * sizeof(double)) + al(sizeof(CgScalars));
+    size_t need = 3 * al(f64) + 4 * al(flo) + (w.mixed ? al(fy) : 0) + al(nblk * sizeof(double)) + al(sizeof(CgScalars));
     void *base = nullptr;
     tm_status st = tm_ctx_workspace(ctx, need, &base);
     if (st != TM_OK) return st;
@@ -487,7 +472,6 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     w.q_hi = take(f64);
     w.r = take(flo);
     w.p = take(flo);
-    w.Ap = take(flo);
     w.q = take(flo);
     w.t = take(flo);
     w.y = w.mixed ? take(fy) : x_dev;   // plain FP64: the update adds straight into x
