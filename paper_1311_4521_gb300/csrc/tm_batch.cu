@@ -386,11 +386,6 @@ using namespace twm;
 
 namespace {
 
-tm_status bfail(tm_ctx *ctx, tm_status st, const std::string &msg)
-{
-    if (ctx) ctx->err = msg;
-    return st;
-}
 
 tm_status bcuda(tm_ctx *ctx, cudaError_t e, const char *where)
 {
@@ -398,7 +393,6 @@ tm_status bcuda(tm_ctx *ctx, cudaError_t e, const char *where)
     return TM_ERR_CUDA;
 }
 
-size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
 
 // Groups the systems by gauge handle (first appearance order) and fills the
 // group templates; order[k] is the caller's index of batch position k.
@@ -406,7 +400,7 @@ tm_status group_systems(tm_ctx *ctx, int nsys, const tm_gauge *const *U, std::ve
                         std::vector<std::vector<int>> &members)
 {
     for (int k = 0; k < nsys; ++k) {
-        if (!U[k]) return bfail(ctx, TM_ERR_ARG, "batch: null gauge handle");
+        if (!U[k]) return tm_fail(ctx, TM_ERR_ARG, "batch: null gauge handle");
         size_t g = 0;
         while (g < handles.size() && handles[g] != U[k]) ++g;
         if (g == handles.size()) {
@@ -424,8 +418,8 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
                                   const void *const *in_e, double kappa, double mu, int sign, void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (nsys < 1 || !U || !out_e || !in_e) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad arguments");
-    if (sign != 1 && sign != -1) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: sign must be +1 or -1");
+    if (nsys < 1 || !U || !out_e || !in_e) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad arguments");
+    if (sign != 1 && sign != -1) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: sign must be +1 or -1");
     std::vector<const tm_gauge *> handles;
     std::vector<std::vector<int>> members;
     tm_status st = group_systems(ctx, nsys, U, handles, members);
@@ -433,14 +427,14 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     const int prec = handles[0]->prec, recon = handles[0]->recon;
     for (auto *h : handles)
         if (h->prec != prec || h->recon != recon)
-            return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_Qtm_batch: all gauge handles need the same precision and reconstruction");
+            return tm_fail(ctx, TM_ERR_UNSUPPORTED, "tm_Qtm_batch: all gauge handles need the same precision and reconstruction");
     for (int k = 0; k < nsys; ++k) {
-        if (bad_ptr(out_e[k]) || bad_ptr(in_e[k]) || out_e[k] == in_e[k]) return bfail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad field pointer");
+        if (bad_ptr(out_e[k]) || bad_ptr(in_e[k]) || out_e[k] == in_e[k]) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad field pointer");
     }
     // workspace: odd temporaries, system table, group table
     size_t need = 0;
-    for (int k = 0; k < nsys; ++k) need += al256(spinor_bytes(U[k]->geom.vh, prec));
-    need += al256(sizeof(BSys) * nsys) + al256(sizeof(BGroup) * handles.size());
+    for (int k = 0; k < nsys; ++k) need += align256(spinor_bytes(U[k]->geom.vh, prec));
+    need += align256(sizeof(BSys) * nsys) + align256(sizeof(BGroup) * handles.size());
     void *base = nullptr;
     st = tm_ctx_scratch(ctx, need, &base);
     if (st != TM_OK) return st;
@@ -450,7 +444,7 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     std::vector<void *> tmp(nsys);
     for (int k = 0; k < nsys; ++k) {
         tmp[k] = c;
-        c += al256(spinor_bytes(U[k]->geom.vh, prec));
+        c += align256(spinor_bytes(U[k]->geom.vh, prec));
     }
     for (size_t g = 0; g < handles.size(); ++g) {
         BGroup G{};
@@ -469,7 +463,7 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
         }
     }
     BSys *dsys = reinterpret_cast<BSys *>(c);
-    c += al256(sizeof(BSys) * nsys);
+    c += align256(sizeof(BSys) * nsys);
     BGroup *dgrp = reinterpret_cast<BGroup *>(c);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(dsys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
@@ -495,9 +489,9 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
 {
     auto t_start = std::chrono::steady_clock::now();
     if (!ctx) return TM_ERR_ARG;
-    if (nsys < 1 || !U_hi || !x_dev || !b_dev || !prm) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad arguments");
+    if (nsys < 1 || !U_hi || !x_dev || !b_dev || !prm) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad arguments");
     if (!(prm->tol > 0.0) || prm->maxiter < 0 || prm->reliable_every < 1 || !(prm->reliable_delta < 1.0))
-        return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad solver parameters");
+        return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad solver parameters");
     std::vector<const tm_gauge *> handles;
     std::vector<std::vector<int>> members;
     tm_status st = group_systems(ctx, nsys, U_hi, handles, members);
@@ -505,21 +499,21 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
     // inner handles: one per group, same precision everywhere
     std::vector<const tm_gauge *> lo(handles.size());
     for (size_t g = 0; g < handles.size(); ++g) {
-        if (handles[g]->prec != TM_F64) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi must be FP64 handles");
+        if (handles[g]->prec != TM_F64) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi must be FP64 handles");
         for (int k : members[g]) {
             const tm_gauge *l = (U_lo && U_lo[k]) ? U_lo[k] : U_hi[k];
-            if (lo[g] && lo[g] != l) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: systems sharing U_hi need the same U_lo");
+            if (lo[g] && lo[g] != l) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: systems sharing U_hi need the same U_lo");
             lo[g] = l;
             if (memcmp(l->dims, handles[g]->dims, sizeof l->dims) || memcmp(l->bc, handles[g]->bc, sizeof l->bc))
-                return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi and U_lo describe different lattices");
-            if (bad_ptr(x_dev[k]) || bad_ptr(b_dev[k]) || x_dev[k] == b_dev[k]) return bfail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad field pointer");
+                return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi and U_lo describe different lattices");
+            if (bad_ptr(x_dev[k]) || bad_ptr(b_dev[k]) || x_dev[k] == b_dev[k]) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad field pointer");
         }
     }
     for (size_t g = 0; g < handles.size(); ++g)
         if (lo[g]->prec != lo[0]->prec || lo[g]->recon != lo[0]->recon || handles[g]->recon != handles[0]->recon)
-            return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_cg_QdagQ_batch: all systems need the same storage formats");
+            return tm_fail(ctx, TM_ERR_UNSUPPORTED, "tm_cg_QdagQ_batch: all systems need the same storage formats");
     if (lo[0]->prec == TM_F64X)
-        return bfail(ctx, TM_ERR_UNSUPPORTED, "tm_cg_QdagQ_batch: TM_F64X inner handles are not supported");
+        return tm_fail(ctx, TM_ERR_UNSUPPORTED, "tm_cg_QdagQ_batch: TM_F64X inner handles are not supported");
 
     Batch B;
     B.nsys = nsys;
@@ -534,16 +528,16 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
     size_t need = 0;
     for (int k = 0; k < nsys; ++k) {
         unsigned vh = U_hi[k]->geom.vh;
-        size_t fl = al256(spinor_bytes(vh, B.P)), fy = al256(spinor_bytes(vh, B.PY)), f64 = al256(spinor_bytes(vh, F64));
-        sys_bytes[k] = 5 * fl + fy + 3 * f64 + al256(sizeof(double) * (vh / 16 + 2)) + al256(sizeof(CgScalars));
+        size_t fl = align256(spinor_bytes(vh, B.P)), fy = align256(spinor_bytes(vh, B.PY)), f64 = align256(spinor_bytes(vh, F64));
+        sys_bytes[k] = 5 * fl + fy + 3 * f64 + align256(sizeof(double) * (vh / 16 + 2)) + align256(sizeof(CgScalars));
         need += sys_bytes[k];
     }
-    need += al256(sizeof(BSys) * nsys) + 2 * al256(sizeof(BGroup) * handles.size()) + al256(sizeof(unsigned) * (nsys + 1));
+    need += align256(sizeof(BSys) * nsys) + 2 * align256(sizeof(BGroup) * handles.size()) + align256(sizeof(unsigned) * (nsys + 1));
     void *base = nullptr;
     st = tm_ctx_workspace(ctx, need, &base);
     if (st != TM_OK) return st;
     char *c = static_cast<char *>(base);
-    auto take = [&](size_t n) { void *p = c; c += al256(n); return p; };
+    auto take = [&](size_t n) { void *p = c; c += align256(n); return p; };
 
     std::vector<BSys> hs;
     std::vector<BGroup> tl, th;

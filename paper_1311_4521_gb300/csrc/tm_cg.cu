@@ -397,11 +397,6 @@ struct Solver {
 
 using namespace twm;
 
-static tm_status cg_fail(tm_ctx *ctx, tm_status st, const char *msg)
-{
-    if (ctx) ctx->err = msg;
-    return st;
-}
 
 static tm_status cg_cuda(tm_ctx *ctx, cudaError_t e, const char *where)
 {
@@ -431,16 +426,16 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
 {
     auto t_start = std::chrono::steady_clock::now();
     if (!ctx) return TM_ERR_ARG;
-    if (!U_hi || bad_ptr(x_dev) || bad_ptr(b_dev) || !prm) return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: null or misaligned pointer");
+    if (!U_hi || bad_ptr(x_dev) || bad_ptr(b_dev) || !prm) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: null or misaligned pointer");
     if (U_hi->prec != TM_F64 && U_hi->prec != TM_F64X)
-        return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi must be an FP64 or FP64X handle");
+        return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi must be an FP64 or FP64X handle");
     if (!U_lo) U_lo = U_hi;
     if (memcmp(U_lo->dims, U_hi->dims, sizeof U_hi->dims) || memcmp(U_lo->bc, U_hi->bc, sizeof U_hi->bc))
-        return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi and U_lo describe different lattices");
+        return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: U_hi and U_lo describe different lattices");
     if (!(prm->tol > 0.0) || prm->maxiter < 0 || prm->reliable_every < 1 || !(prm->reliable_delta < 1.0))
-        return cg_fail(ctx, TM_ERR_ARG,
+        return tm_fail(ctx, TM_ERR_ARG,
                        "tm_cg_QdagQ: need tol > 0, maxiter >= 0, reliable_every >= 1, reliable_delta < 1");
-    if (x_dev == b_dev) return cg_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: x and b must not overlap");
+    if (x_dev == b_dev) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ: x and b must not overlap");
 
     Solver S;
     S.Uh = U_hi;
@@ -457,14 +452,13 @@ extern "C" tm_status tm_cg_QdagQ(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
 
     // workspace: FP64 ax, t_hi, q_hi (+ r in plain mode), inner r, p, q, t, y, partials, scalars
     const size_t f64 = spinor_bytes(w.vh, w.PH), flo = spinor_bytes(w.vh, w.P), fy = spinor_bytes(w.vh, w.PY);
-    auto al = [](size_t n) { return (n + 255) & ~size_t(255); };
     const size_t nblk = blocks(w.vh, 128) + 1;
-    size_t need = 3 * al(f64) + 4 * al(flo) + (w.mixed ? al(fy) : 0) + al(nblk * sizeof(double)) + al(sizeof(CgScalars));
+    size_t need = 3 * align256(f64) + 4 * align256(flo) + (w.mixed ? align256(fy) : 0) + align256(nblk * sizeof(double)) + align256(sizeof(CgScalars));
     void *base = nullptr;
     tm_status st = tm_ctx_workspace(ctx, need, &base);
     if (st != TM_OK) return st;
     char *c = static_cast<char *>(base);
-    auto take = [&](size_t n) { void *p = c; c += al(n); return p; };
+    auto take = [&](size_t n) { void *p = c; c += align256(n); return p; };
     w.x = x_dev;
     w.b = const_cast<void *>(b_dev);
     w.ax = take(f64);

@@ -165,9 +165,9 @@ extern "C" tm_status tm_force_ex(tm_ctx *ctx, const tm_gauge *U, double *F_dev, 
         return TM_ERR_UNSUPPORTED;
     }
     const unsigned vh = U->geom.vh;
-    const size_t fb = (spinor_bytes(vh, U->prec) + 255) & ~size_t(255);
+    const size_t fb = align256(spinor_bytes(vh, U->prec));
     const size_t nF = size_t(4) * 2 * vh * 18;   // doubles in one force field
-    const size_t hb = scheme == TM_FORCE_HALO ? (nF * sizeof(double) + 255) & ~size_t(255) : 0;
+    const size_t hb = scheme == TM_FORCE_HALO ? align256(nF * sizeof(double)) : 0;
     void *base = nullptr;
     tm_status st = tm_ctx_workspace(ctx, 3 * fb + 2 * hb, &base);
     if (st != TM_OK) return st;

@@ -18,14 +18,6 @@ using namespace twm;
 
 namespace {
 
-tm_status host_fail(tm_ctx *ctx, tm_status st, const std::string &msg)
-{
-    ctx->err = msg;
-    return st;
-}
-
-size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
-
 tm_status grow_stage(tm_ctx *ctx, size_t bytes)
 {
     if (ctx->stage_bytes >= bytes) return TM_OK;
@@ -33,12 +25,12 @@ tm_status grow_stage(tm_ctx *ctx, size_t bytes)
         cudaError_t e = cudaFree(ctx->stage);
         ctx->stage = nullptr;
         ctx->stage_bytes = 0;
-        if (e != cudaSuccess) return host_fail(ctx, TM_ERR_CUDA, std::string("cudaFree(stage): ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) return tm_fail(ctx, TM_ERR_CUDA, std::string("cudaFree(stage): ") + cudaGetErrorString(e));
     }
     cudaError_t e = cudaMalloc(&ctx->stage, bytes);
     if (e != cudaSuccess) {
         ctx->stage = nullptr;
-        return host_fail(ctx, TM_ERR_CUDA, std::string("cudaMalloc(stage): ") + cudaGetErrorString(e));
+        return tm_fail(ctx, TM_ERR_CUDA, std::string("cudaMalloc(stage): ") + cudaGetErrorString(e));
     }
     ctx->stage_bytes = bytes;
     return TM_OK;
@@ -71,19 +63,19 @@ extern "C" tm_status tm_Qtm_host(tm_ctx *ctx, const tm_gauge *U, int n, double *
                                  const double *const *in_host, double kappa, double mu, int sign, void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!U || n < 1 || !out_host || !in_host) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: bad arguments");
-    if (sign != 1 && sign != -1) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: sign must be +1 or -1");
+    if (!U || n < 1 || !out_host || !in_host) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: bad arguments");
+    if (sign != 1 && sign != -1) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: sign must be +1 or -1");
     std::set<const void *> ins;
     for (int k = 0; k < n; ++k) {
-        if (!out_host[k] || !in_host[k]) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: null field pointer");
+        if (!out_host[k] || !in_host[k]) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: null field pointer");
         ins.insert(in_host[k]);
     }
     for (int k = 0; k < n; ++k)
-        if (ins.count(out_host[k])) return host_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: an output buffer is also an input");
+        if (ins.count(out_host[k])) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_host: an output buffer is also an input");
 
     const unsigned vh = U->geom.vh;
     const size_t cb = size_t(vh) * 24 * sizeof(double);  // canonical complex double [Vh][4][3]
-    const size_t cba = al256(cb), pba = al256(spinor_bytes(vh, U->prec));
+    const size_t cba = align256(cb), pba = align256(spinor_bytes(vh, U->prec));
     tm_status st = grow_stage(ctx, 2 * (2 * cba + 2 * pba));
     if (st != TM_OK) return st;
     void *tmp = nullptr;  // tm_Qtm's scratch, grown now so that no call below reallocates it
@@ -104,7 +96,7 @@ extern "C" tm_status tm_Qtm_host(tm_ctx *ctx, const tm_gauge *U, int n, double *
     if (e == cudaSuccess && !ctx->copy_out) e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking);
     SlotEvents ev;
     if (e == cudaSuccess) e = ev.create();
-    if (e != cudaSuccess) return host_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_host: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_host: ") + cudaGetErrorString(e));
 
     cudaStream_t s = (cudaStream_t)stream, ci = ctx->copy_in, co = ctx->copy_out;
     st = TM_OK;
@@ -133,6 +125,6 @@ extern "C" tm_status tm_Qtm_host(tm_ctx *ctx, const tm_gauge *U, int n, double *
     cudaError_t e3 = cudaStreamSynchronize(co);
     if (st != TM_OK) return st;
     if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
-    if (e != cudaSuccess) return host_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_host: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_host: ") + cudaGetErrorString(e));
     return TM_OK;
 }

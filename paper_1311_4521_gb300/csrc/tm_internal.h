@@ -30,6 +30,17 @@ struct tm_ctx {
     cudaStream_t copy_out = nullptr;
 };
 
+// Records msg as the context's last error (tm_last_error) and returns st.
+inline tm_status tm_fail(tm_ctx *ctx, tm_status st, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+// n rounded up to a multiple of 256 bytes, the alignment of every
+// sub-buffer carved out of a workspace.
+constexpr size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
 // Records trace event k of ctx on stream s, if tracing is on.
 // A device pointer that the kernels may read or write with 16-byte vector
 // accesses: non-null and 16-byte aligned (a misaligned vector access would

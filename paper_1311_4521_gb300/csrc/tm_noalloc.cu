@@ -34,19 +34,13 @@ constexpr int kMaxDevices = 128;
 std::mutex g_lock;
 void *g_scratch_addr[kMaxDevices] = {};
 
-tm_status noalloc_fail(tm_ctx *ctx, tm_status st, const std::string &msg)
-{
-    if (ctx) ctx->err = msg;
-    return st;
-}
-
 // Device address of g_qtm_scratch on the context's device, looked up once
 // per device with that device current (the caller's current device is
 // restored afterwards).
 tm_status scratch_address(tm_ctx *ctx, void **addr)
 {
     if (ctx->device < 0 || ctx->device >= kMaxDevices)
-        return noalloc_fail(ctx, TM_ERR_UNSUPPORTED, "tm_Qtm_noalloc: device index out of range");
+        return tm_fail(ctx, TM_ERR_UNSUPPORTED, "tm_Qtm_noalloc: device index out of range");
     std::lock_guard<std::mutex> guard(g_lock);
     if (!g_scratch_addr[ctx->device]) {
         int cur = -1;
@@ -59,7 +53,7 @@ tm_status scratch_address(tm_ctx *ctx, void **addr)
             if (e == cudaSuccess) e = e2;
         }
         if (e != cudaSuccess)
-            return noalloc_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_noalloc: cudaGetSymbolAddress: ") +
+            return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_noalloc: cudaGetSymbolAddress: ") +
                                                       cudaGetErrorString(e));
         g_scratch_addr[ctx->device] = p;
     }
@@ -73,9 +67,9 @@ extern "C" tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_
                                     double kappa, double mu, int sign, void *stream)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (!U || bad_ptr(out_e_dev) || bad_ptr(in_e_dev)) return noalloc_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: null or misaligned pointer");
-    if (sign != 1 && sign != -1) return noalloc_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: sign must be +1 or -1");
-    if (out_e_dev == in_e_dev) return noalloc_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: out and in must not overlap");
+    if (!U || bad_ptr(out_e_dev) || bad_ptr(in_e_dev)) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: null or misaligned pointer");
+    if (sign != 1 && sign != -1) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: sign must be +1 or -1");
+    if (out_e_dev == in_e_dev) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_noalloc: out and in must not overlap");
     size_t need = spinor_bytes(U->geom.vh, U->prec);
     if (need > size_t(TM_QTM_NOALLOC_MAX_BYTES)) {
         char buf[256];
@@ -83,7 +77,7 @@ extern "C" tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_
                  "tm_Qtm_noalloc: the odd temporary needs %zu bytes, more than the %zu-byte static scratch "
                  "array; use tm_Qtm for this lattice and precision",
                  need, size_t(TM_QTM_NOALLOC_MAX_BYTES));
-        return noalloc_fail(ctx, TM_ERR_ARG, buf);
+        return tm_fail(ctx, TM_ERR_ARG, buf);
     }
     void *tmp = nullptr;
     tm_status st = scratch_address(ctx, &tmp);
@@ -96,6 +90,6 @@ extern "C" tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_
         e = launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, tmp, out_e_dev, in_e_dev,
                        coef_qtm_b_unit(mut), s, 128);
     if (e != cudaSuccess)
-        return noalloc_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_noalloc: launch: ") + cudaGetErrorString(e));
+        return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_noalloc: launch: ") + cudaGetErrorString(e));
     return TM_OK;
 }

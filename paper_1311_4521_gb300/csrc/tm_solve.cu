@@ -50,7 +50,7 @@ extern "C" tm_status tm_solve_eo(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
         return TM_ERR_ARG;
     }
     const Geom &g = U_hi->geom;
-    const size_t fb = (spinor_bytes(g.vh, F64) + 255) & ~size_t(255);
+    const size_t fb = align256(spinor_bytes(g.vh, F64));
     void *base = nullptr;
     tm_status st = tm_ctx_scratch(ctx, 3 * fb, &base);
     if (st != TM_OK) return st;
