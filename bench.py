@@ -83,6 +83,16 @@ def hop_bytes(prec: str, recon: int) -> int:
     return b + (8 if prec == "f16" else 0)           # per-site norms of the f16 spinors
 
 
+def workload_config(dims, prec: str, recon: int, world: int) -> dict:
+    """The `config` of the JSON line: the workload one step processes."""
+    vh = int(np.prod(dims)) // 2
+    return {"workload": f"Q_tm, {'x'.join(str(d) for d in dims)}, {prec} storage, {recon}-real links, "
+                        "U=exp(0.3iA), kappa=0.1394, mu=0.0015, antiperiodic t",
+            "lattice": list(dims), "even_sites": vh, "storage": prec, "reconstruct": recon,
+            "bytes_per_step": vh * algo_bytes(prec, recon)["qtm"], "flops_per_step": vh * QTM_FLOPS,
+            "parallelism": f"replicas x{world}"}
+
+
 def algo_bytes(prec: str, recon: int) -> dict:
     reread = 24 * REAL[prec] + (4 if prec == "f16" else 0)
     a = hop_bytes(prec, recon)
@@ -408,13 +418,9 @@ def gpu_arm(args) -> None:
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
-            "config": {"workload": f"Q_tm, {'x'.join(str(d) for d in DIMS)}, {prec} storage, {recon}-real links, "
-                                   "U=exp(0.3iA), kappa=0.1394, mu=0.0015, antiperiodic t",
-                       "lattice": list(DIMS), "even_sites": vh, "storage": prec, "reconstruct": recon,
-                       "bytes_per_step": vh * ab["qtm"], "flops_per_step": vh * QTM_FLOPS,
-                       "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 ({links_gb:.2f} GB links "
-                             f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"},
+            "config": dict(workload_config(DIMS, prec, recon, world),
+                           l2=f"inputs larger than L2 ({links_gb:.2f} GB links "
+                              f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"),
             "gflops": round(gflops, 2), "roofline": roofline, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
             "cpu_baseline": cpu,
@@ -708,13 +714,13 @@ def reference_arm(args) -> None:
     ab = algo_bytes("f64", 18)
     value = vh * ab["qtm"] / dt / 1e9
     cores = int(os.environ["OMP_NUM_THREADS"])
-    sample = f"one Q_tm per step on a 16^4 lattice (same link distribution, kappa, mu; FP64)"
+    sample = ("one Q_tm per step on a 16^4 sample lattice of the workload (same link distribution, kappa, "
+              "mu; FP64), its GB/s scaled per site to the workload's bytes")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "Q_tm, FP64, 18-real links, U=exp(0.3iA), kappa=0.1394, mu=0.0015 "
-                               "(16^4 sample of the 32^3x64 workload)", "lattice": list(SAMPLE_DIMS)},
+        "config": dict(workload_config(args.lattice, "f64", 18, args.gpus), sample_lattice=list(SAMPLE_DIMS)),
         "gflops": round(vh * QTM_FLOPS / dt / 1e9, 3),
         "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
