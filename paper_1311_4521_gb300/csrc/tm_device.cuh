@@ -43,7 +43,13 @@
 #ifndef TM_HOP_MINB_F64X
 #define TM_HOP_MINB_F64X 3
 #endif
-#define TM_HOP_MINB(P) ((P) == 0 ? 2 : (P) == 3 ? TM_HOP_MINB_F64X : (P) == 1 ? TM_HOP_MINB_F32 : TM_HOP_MINB_F16)
+#ifndef TM_HOP_MINB_F64
+#define TM_HOP_MINB_F64 2
+#endif
+#ifndef TM_F64X_UNROLL
+#define TM_F64X_UNROLL 2  // hops per iteration of the double-float stencil loop (sweep of 1, 2, 4)
+#endif
+#define TM_HOP_MINB(P) ((P) == 0 ? TM_HOP_MINB_F64 : (P) == 3 ? TM_HOP_MINB_F64X : (P) == 1 ? TM_HOP_MINB_F32 : TM_HOP_MINB_F16)
 
 namespace twm {
 
@@ -808,10 +814,11 @@ TM_HD void hop_dir_pair(const Geom &g, const Nbrs &n, const Src &src, const void
         }
 }
 
-// The 8 hops as a loop that is not unrolled, for double-float storage: its
-// arithmetic expands to so many FP32 instructions that the fully unrolled
-// stencil overflows the instruction cache (ncu: warps stalled on
-// "no instruction").  Each link multiply is instantiated once; the
+// The 8 hops as a loop unrolled only by TM_F64X_UNROLL, for double-float
+// storage: its arithmetic expands to so many FP32 instructions that the
+// fully unrolled stencil overflows the instruction cache (ncu: warps stalled
+// on "no instruction"); two hops per iteration were measured 2 % faster
+// than one, four slower.  Each link multiply is instantiated once; the
 // direction-dependent spin algebra is selected by small switches, and all
 // register arrays keep static indices.
 template <int P, bool DAG, class Src>
@@ -821,7 +828,8 @@ TM_HD void hop_site_rolled(const Geom &g, const Nbrs &n, const Src &src, const v
     using R = typename SpinorIO<P>::R;
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-#pragma unroll 1
+    constexpr int kUnroll = TM_F64X_UNROLL;
+#pragma unroll kUnroll
     for (int k = 0; k < 8; ++k) {
         const int mu = k >> 1;
         const bool fwd = (k & 1) == 0;
