@@ -41,17 +41,18 @@ __device__ __forceinline__ int find_sys(const unsigned *item0, int nsys, unsigne
     return k;
 }
 
-// Block sum of v over BLA threads in a fixed order; the result is valid in thread 0.
+// Block sum of v over BLA threads in a fixed order (warp sums, then the
+// BLA / 32 warp results in order); the result is valid in thread 0.  Every
+// thread of the block must call it.
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
-    red[threadIdx.x] = v;
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    for (int w = BLA / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < unsigned(w)) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    double r = red[0];
-    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < BLA / 32; ++w) r += red[w];
+    __syncthreads();  // red is reused by the caller's next item
     return r;
 }
 
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_update(const BS
 {
     using R = typename SpinorIO<P>::R;
     using RY = typename SpinorIO<PY>::R;
-    __shared__ double red[BLA];
+    __shared__ double red[BLA / 32];
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int k = find_sys(item0, nsys, item);
         const BSys &S = sys[k];
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(BLA, 3) k_batch_residual(const BSys *__restric
                                                         unsigned nitems, int gate)
 {
     using R = typename SpinorIO<P>::R;
-    __shared__ double red[BLA];
+    __shared__ double red[BLA / 32];
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int k = find_sys(item0, nsys, item);
         const BSys &S = sys[k];
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(BLA, 3) k_batch_residual(const BSys *__restric
 __global__ void __launch_bounds__(BLA, 4) k_batch_norm(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
                                                     unsigned nitems, int role)
 {
-    __shared__ double red[BLA];
+    __shared__ double red[BLA / 32];
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int k = find_sys(item0, nsys, item);
         const BSys &S = sys[k];
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(BLA, 4) k_batch_zero(const BSys *__restrict__ 
 __global__ void __launch_bounds__(BLA, 4) k_batch_finish(const BSys *__restrict__ sys, int nsys, unsigned tile_sites, int op,
                                                       int gate)
 {
-    __shared__ double red[BLA];
+    __shared__ double red[BLA / 32];
     const BSys &S = sys[blockIdx.x];
     if (gated(S.s, gate)) return;
     const unsigned n = (S.vh + tile_sites - 1) / tile_sites;

@@ -27,6 +27,14 @@ struct BGroup {
 constexpr int BT = 128;   // threads per CTA of the batched hop
 constexpr int BLA = 256;  // threads per CTA of the batched vector kernels
 
+// Sum of v over the 32 lanes of a warp in a fixed order (valid in lane 0).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ int find_group(const BGroup *gr, int ng, unsigned item)
 {
     int gi = 0;
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
     constexpr int TS = NRB > 1 ? BT / NRB : BT;
     __shared__ V tile[NRB > 1 ? 8 * L::NCHUNK * TS : 1];
     __shared__ unsigned bwd_idx[NRB > 1 ? 4 * TS : 1];
-    __shared__ double red[BT];
+    __shared__ double red[BT / 32];
     const unsigned tx = threadIdx.x % TS, ty = threadIdx.x / TS;
 
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
@@ -134,12 +142,15 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
                 if (NORM) nrm = norm2(o);
             }
             if (NORM) {
-                // one partial per (system, tile): the TS threads of each right-hand side, summed in order
-                red[threadIdx.x] = nrm;
+                // one partial per (system, tile): each warp sums its lanes, then the
+                // TS / 32 warps of each right-hand side are added in order
+                static_assert(TS % 32 == 0, "a warp must not span two right-hand sides");
+                const double ws = warp_sum(nrm);
+                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;
                 __syncthreads();
                 if (tx == 0 && active) {
                     double sum = 0.0;
-                    for (int t = 0; t < TS; ++t) sum += red[ty * TS + t];
+                    for (int w = 0; w < TS / 32; ++w) sum += red[(ty * TS) / 32 + w];
                     S->partials[tno] = sum;
                 }
                 __syncthreads();
