@@ -56,47 +56,6 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return r;
 }
 
-// y += alpha p, r -= alpha Ap, partial |r|^2
-template <int P, int PY>
-__global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_update(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
-                                                      unsigned nitems, int gate)
-{
-    using R = typename SpinorIO<P>::R;
-    using RY = typename SpinorIO<PY>::R;
-    __shared__ double red[BLA / 32];
-    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int k = find_sys(item0, nsys, item);
-        const BSys &S = sys[k];
-        if (gated(S.s, gate)) continue;   // uniform over the block
-        const unsigned tno = item - item0[k], i = tno * BLA + threadIdx.x;
-        double nrm = 0.0;
-        if (i < S.vh) {
-            const R a = to_R<R>(S.s->alpha);
-            const RY ay = to_R<RY>(S.s->alpha);
-            Spinor<R> pv, av, rv;
-            Spinor<RY> yv;
-            SpinorIO<P>::load(S.f[R_P], S.vh, i, pv);
-            SpinorIO<P>::load(S.f[R_AP], S.vh, i, av);
-            SpinorIO<P>::load(S.f[R_R], S.vh, i, rv);
-            SpinorIO<PY>::load(S.f[R_Y], S.vh, i, yv);
-#pragma unroll
-            for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    yv[sp][c].re += ay * RY(pv[sp][c].re);
-                    yv[sp][c].im += ay * RY(pv[sp][c].im);
-                    rv[sp][c].re -= a * av[sp][c].re;
-                    rv[sp][c].im -= a * av[sp][c].im;
-                }
-            SpinorIO<PY>::store(S.f[R_Y], S.vh, i, yv);
-            SpinorIO<P>::store(S.f[R_R], S.vh, i, rv);
-            nrm = norm2(rv);
-        }
-        double sum = block_sum(nrm, red);
-        if (threadIdx.x == 0) S.partials[tno] = sum;
-    }
-}
-
 // p = r + beta p (restart: p = r)
 template <int P>
 __global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_pupdate(const BSys *__restrict__ sys, const unsigned *item0, int nsys,
@@ -260,15 +219,15 @@ struct Batch {
 unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
 
 cudaError_t bhop(int prec, int recon, const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx,
-                 const Coef &k, bool norm, int gate, cudaStream_t st)
+                 const Coef &k, int mode, int gate, cudaStream_t st)
 {
     if (t.nitems == 0) return cudaSuccess;
     switch (prec * 100 + recon) {
-    case F64 * 100 + 18: return batch_hop_f64(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F64X * 100 + 18: return batch_hop_f64x(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F32 * 100 + 12: return batch_hop_f32_12(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F32 * 100 + 18: return batch_hop_f32_18(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case F16 * 100 + 12: return batch_hop_f16(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case F64 * 100 + 18: return batch_hop_f64(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case F64X * 100 + 18: return batch_hop_f64x(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case F32 * 100 + 12: return batch_hop_f32_12(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case F32 * 100 + 18: return batch_hop_f32_18(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case F16 * 100 + 12: return batch_hop_f16(t, sys, parity, rin, rout, rx, k, mode, gate, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -315,11 +274,11 @@ float time_table(int prec, int recon, const HopTable &t, const BSys *sys, int ri
     cudaEvent_t ev[4];
     for (auto &e : ev) cudaEventCreate(&e);
     Coef k = coef_plain();
-    bhop(prec, recon, t, sys, 1, rin, rout, -1, k, false, 0, st);
+    bhop(prec, recon, t, sys, 1, rin, rout, -1, k, BH_PLAIN, 0, st);
     float ms[3] = {0.f, 0.f, 0.f};
     cudaEventRecord(ev[0], st);
     for (int round = 0; round < 3; ++round) {
-        for (int r = 0; r < 3; ++r) bhop(prec, recon, t, sys, 1, rin, rout, -1, k, false, 0, st);
+        for (int r = 0; r < 3; ++r) bhop(prec, recon, t, sys, 1, rin, rout, -1, k, BH_PLAIN, 0, st);
         cudaEventRecord(ev[round + 1], st);
     }
     cudaEventSynchronize(ev[3]);
@@ -473,9 +432,9 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: setup");
     const double mut = 2.0 * kappa * mu * sign;
     tm_trace_mark(ctx, 0, s);
-    e = bhop(prec, recon, t, dsys, 1, R_IN, R_T, -1, coef_qtm_a_scaled(kappa, mut), false, 0, s);
+    e = bhop(prec, recon, t, dsys, 1, R_IN, R_T, -1, coef_qtm_a_scaled(kappa, mut), BH_PLAIN, 0, s);
     tm_trace_mark(ctx, 1, s);
-    if (e == cudaSuccess) e = bhop(prec, recon, t, dsys, 0, R_T, R_OUT, R_IN, coef_qtm_b_unit(mut), false, 0, s);
+    if (e == cudaSuccess) e = bhop(prec, recon, t, dsys, 0, R_T, R_OUT, R_IN, coef_qtm_b_unit(mut), BH_PLAIN, 0, s);
     tm_trace_mark(ctx, 2, s);
     if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: launch");
     // the tables live in scratch: keep them until the launches have read them
@@ -524,13 +483,13 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
     B.recon_hi = handles[0]->recon;
     B.PY = B.P == F16 ? F32 : B.P;
 
-    // workspace per system: inner r, p, Ap, q, t; y; FP64 ax, t_hi, q_hi; partials; scalars
+    // workspace per system: inner r, p, q, t; y; FP64 ax, t_hi, q_hi; partials; scalars
     std::vector<size_t> sys_bytes(nsys);
     size_t need = 0;
     for (int k = 0; k < nsys; ++k) {
         unsigned vh = U_hi[k]->geom.vh;
         size_t fl = align256(spinor_bytes(vh, B.P)), fy = align256(spinor_bytes(vh, B.PY)), f64 = align256(spinor_bytes(vh, F64));
-        sys_bytes[k] = 5 * fl + fy + 3 * f64 + align256(sizeof(double) * (vh / 16 + 2)) + align256(sizeof(CgScalars));
+        sys_bytes[k] = 4 * fl + fy + 3 * f64 + align256(sizeof(double) * (vh / 16 + 2)) + align256(sizeof(CgScalars));
         need += sys_bytes[k];
     }
     need += align256(sizeof(BSys) * nsys) + 2 * align256(sizeof(BGroup) * handles.size()) + align256(sizeof(unsigned) * (nsys + 1));
@@ -561,7 +520,6 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
             S.f[R_B] = const_cast<void *>(b_dev[k]);
             S.f[R_R] = take(spinor_bytes(vh, B.P));
             S.f[R_P] = take(spinor_bytes(vh, B.P));
-            S.f[R_AP] = take(spinor_bytes(vh, B.P));
             S.f[R_Q] = take(spinor_bytes(vh, B.P));
             S.f[R_T] = take(spinor_bytes(vh, B.P));
             S.f[R_Y] = take(spinor_bytes(vh, B.PY));
@@ -616,10 +574,10 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
     auto hop_tile = [&](const HopTable &t) { return unsigned(t.nrb > 1 ? BT / t.nrb : BT); };
     // ax = Q^dag Q x in FP64 for the systems the gate lets through
     auto qdagq_hi = [&](int gate, cudaStream_t q) {
-        cudaError_t r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_X, R_THI, -1, coef_qtm_a_scaled(kappa, mut), false, gate, q);
-        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_QHI, R_X, coef_qtm_b_unit(mut), false, gate, q);
-        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_QHI, R_THI, -1, coef_qtm_a_scaled(kappa, -mut), false, gate, q);
-        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_AX, R_QHI, coef_qtm_b_unit(-mut), false, gate, q);
+        cudaError_t r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_X, R_THI, -1, coef_qtm_a_scaled(kappa, mut), BH_PLAIN, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_QHI, R_X, coef_qtm_b_unit(mut), BH_PLAIN, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_QHI, R_THI, -1, coef_qtm_a_scaled(kappa, -mut), BH_PLAIN, gate, q);
+        if (r == cudaSuccess) r = bhop(F64, B.recon_hi, B.hi, SY, 0, R_THI, R_AX, R_QHI, coef_qtm_b_unit(-mut), BH_PLAIN, gate, q);
         return r;
     };
     auto residual = [&](int gate, cudaStream_t q) {
@@ -639,17 +597,13 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
         return r;
     };
     auto iteration = [&](cudaStream_t q) {
-        cudaError_t r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_P, R_T, -1, coef_qtm_a_scaled(kappa, mut), false, 1, q);
-        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_Q, R_P, coef_qtm_b_unit(mut), true, 1, q);
+        cudaError_t r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_P, R_T, -1, coef_qtm_a_scaled(kappa, mut), BH_PLAIN, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_Q, R_P, coef_qtm_b_unit(mut), BH_NORM, 1, q);
         if (r == cudaSuccess) r = finish(hop_tile(B.lo), FIN_PAP, 1, q);
-        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_Q, R_T, -1, coef_qtm_a_scaled(kappa, -mut), false, 1, q);
-        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, R_AP, R_Q, coef_qtm_b_unit(-mut), false, 1, q);
-        if (r != cudaSuccess) return r;
-        if (B.P == F64) k_batch_update<F64, F64><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);
-        else if (B.P == F32) k_batch_update<F32, F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);
-        else k_batch_update<F16, F32><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 1);
-        r = cudaGetLastError();
-        if (r == cudaSuccess) r = finish(BLA, FIN_RR_UPDATE, 1, q);
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 1, R_Q, R_T, -1, coef_qtm_a_scaled(kappa, -mut), BH_PLAIN, 1, q);
+        // the last hop of Q^dag Q p applies y += alpha p, r -= alpha Ap itself (Ap is not stored)
+        if (r == cudaSuccess) r = bhop(B.P, B.recon_lo, B.lo, SY, 0, R_T, -1, R_Q, coef_qtm_b_unit(-mut), BH_UPDATE, 1, q);
+        if (r == cudaSuccess) r = finish(hop_tile(B.lo), FIN_RR_UPDATE, 1, q);
         // reliable update where due: x += y, r = b - Q^dag Q x in FP64
         if (r == cudaSuccess) {
             if (B.PY == F64) k_batch_accum<F64><<<G, BLA, 0, q>>>(SY, I0, nsys, NI, 2);

@@ -7,7 +7,7 @@
 
 namespace twm {
 
-enum Role { R_X, R_B, R_R, R_P, R_AP, R_Q, R_T, R_Y, R_AX, R_THI, R_QHI, R_IN, R_OUT, NROLE };
+enum Role { R_X, R_B, R_R, R_P, R_Q, R_T, R_Y, R_AX, R_THI, R_QHI, R_IN, R_OUT, NROLE };
 
 struct BSys {
     void *f[NROLE];
@@ -25,6 +25,12 @@ struct BGroup {
 };
 
 constexpr int BT = 128;   // threads per CTA of the batched hop
+
+// What the batched hop does with its result: store it (PLAIN), store it and
+// reduce |out|^2 per (system, tile) (NORM), or, as the last hop of
+// Q^dag Q p in the CG, apply y += alpha p, r -= alpha out and reduce |r|^2
+// per (system, tile) without storing out (UPDATE).
+enum { BH_PLAIN = 0, BH_NORM = 1, BH_UPDATE = 2 };
 constexpr int BLA = 256;  // threads per CTA of the batched vector kernels
 
 // Sum of v over the 32 lanes of a warp in a fixed order (valid in lane 0).
@@ -53,20 +59,20 @@ struct HopTable {
 
 // Launches of the batched hop for one storage format (tm_batch_hop_*.cu).
 cudaError_t batch_hop_f64(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
-                          bool norm, int gate, cudaStream_t st);
+                          int mode, int gate, cudaStream_t st);
 cudaError_t batch_hop_f64x(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
-                           bool norm, int gate, cudaStream_t st);
+                           int mode, int gate, cudaStream_t st);
 cudaError_t batch_hop_f32_12(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
-                             bool norm, int gate, cudaStream_t st);
+                             int mode, int gate, cudaStream_t st);
 cudaError_t batch_hop_f32_18(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
-                             bool norm, int gate, cudaStream_t st);
+                             int mode, int gate, cudaStream_t st);
 cudaError_t batch_hop_f16(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
-                          bool norm, int gate, cudaStream_t st);
+                          int mode, int gate, cudaStream_t st);
 
 // NRB: 1 streams links, items (tile, rhs) with the right-hand side fastest;
 // 0 the same with default-cached links (L2 sharing); >= 2 stages the tile's
 // links in shared memory and sweeps the right-hand sides NRB at a time.
-template <int P, int RECON, int NRB, bool NORM>
+template <int P, int RECON, int NRB, int MODE>
 __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ groups, int ngroups, unsigned nitems,
                                                   const BSys *__restrict__ sys, int parity, int rin, int rout, int rx,
                                                   Coef k, int gate)
@@ -138,10 +144,35 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
                 } else {
                     epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
                 }
-                SpinorIO<P>::store(S->f[rout], G.g.vh, i, o);
-                if (NORM) nrm = norm2(o);
+                if (MODE == BH_UPDATE) {
+                    constexpr int PY = P == F16 ? F32 : P;
+                    using RY = typename SpinorIO<PY>::R;
+                    const double alpha = S->s->alpha;
+                    Spinor<R> pv, rv;
+                    Spinor<RY> yv;
+                    SpinorIO<P>::load(S->f[R_P], G.g.vh, i, pv);
+                    SpinorIO<P>::load(S->f[R_R], G.g.vh, i, rv);
+                    SpinorIO<PY>::load(S->f[R_Y], G.g.vh, i, yv);
+                    const R a = to_R<R>(alpha);
+                    const RY ay = to_R<RY>(alpha);
+#pragma unroll
+                    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            yv[sp][c].re += ay * RY(pv[sp][c].re);
+                            yv[sp][c].im += ay * RY(pv[sp][c].im);
+                            rv[sp][c].re -= a * o[sp][c].re;
+                            rv[sp][c].im -= a * o[sp][c].im;
+                        }
+                    SpinorIO<PY>::store(S->f[R_Y], G.g.vh, i, yv);
+                    SpinorIO<P>::store(S->f[R_R], G.g.vh, i, rv);
+                    nrm = norm2(rv);
+                } else {
+                    SpinorIO<P>::store(S->f[rout], G.g.vh, i, o);
+                    if (MODE == BH_NORM) nrm = norm2(o);
+                }
             }
-            if (NORM) {
+            if (MODE != BH_PLAIN) {
                 // one partial per (system, tile): each warp sums its lanes, then the
                 // TS / 32 warps of each right-hand side are added in order
                 static_assert(TS % 32 == 0, "a warp must not span two right-hand sides");
@@ -160,31 +191,36 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
 }
 
 template <int P, int RECON, int NRB, bool WITH_NORM = true>
-inline cudaError_t hop_nrb(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
+inline cudaError_t hop_nrb(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, int mode,
                     int gate, cudaStream_t st)
 {
-    if (norm) {
-        if constexpr (WITH_NORM)
-            k_batch_hop<P, RECON, NRB, true><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
-        else
+    if (mode != BH_PLAIN) {
+        if constexpr (WITH_NORM) {
+            if (mode == BH_NORM)
+                k_batch_hop<P, RECON, NRB, BH_NORM><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+            else
+                k_batch_hop<P, RECON, NRB, BH_UPDATE><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+        } else {
             return cudaErrorInvalidValue;
-    } else
-        k_batch_hop<P, RECON, NRB, false><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+        }
+    } else {
+        k_batch_hop<P, RECON, NRB, BH_PLAIN><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+    }
     return cudaGetLastError();
 }
 
 template <int P, int RECON, bool WITH_NORM = true>
-inline cudaError_t hop_pr(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, bool norm,
+inline cudaError_t hop_pr(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, int mode,
                    int gate, cudaStream_t st)
 {
     switch (t.nrb) {
-    case 0: return hop_nrb<P, RECON, 0, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
-    case 1: return hop_nrb<P, RECON, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case 0: return hop_nrb<P, RECON, 0, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case 1: return hop_nrb<P, RECON, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
     case 2:
         // 8-byte-per-real tiles of 64 sites would exceed 48 KB of static shared memory
-        if constexpr (P != F64 && P != F64X) return hop_nrb<P, RECON, 2, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+        if constexpr (P != F64 && P != F64X) return hop_nrb<P, RECON, 2, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
         return cudaErrorInvalidValue;
-    case 4: return hop_nrb<P, RECON, 4, WITH_NORM>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    case 4: return hop_nrb<P, RECON, 4, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -5,9 +5,9 @@
 namespace twm {
 
 cudaError_t batch_hop_f64(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
-                        bool norm, int gate, cudaStream_t st)
+                        int mode, int gate, cudaStream_t st)
 {
-    return hop_pr<F64, 18>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    return hop_pr<F64, 18>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
 }
 
 }  // namespace twm

@@ -5,10 +5,10 @@
 namespace twm {
 
 cudaError_t batch_hop_f64x(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
-                        bool norm, int gate, cudaStream_t st)
+                        int mode, int gate, cudaStream_t st)
 {
     // no batched solver runs its inner iteration in this format: no fused norm
-    return hop_pr<F64X, 18, false>(t, sys, parity, rin, rout, rx, k, norm, gate, st);
+    return hop_pr<F64X, 18, false>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
 }
 
 }  // namespace twm
