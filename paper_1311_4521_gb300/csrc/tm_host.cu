@@ -4,10 +4,12 @@
 // service that receives right-hand sides from elsewhere) pays, per
 // application, a host-to-device copy of the input, the operator and a
 // device-to-host copy of the result.  tm_Qtm_host takes a list of such
-// fields and pipelines them through two device staging slots: while field
-// k is packed, multiplied and unpacked on the compute stream, field k+1 is
-// copied in on one copy stream and field k-1 copied out on another.  With
-// pinned host memory the copies then hide behind the kernels.  Every copy is
+// fields and pipelines them through two device staging slots: while the
+// operator of field k runs on the compute stream, field k+1 is copied in
+// and packed on one copy stream and field k-1 unpacked and copied out on
+// another.  The operator in FP64 is bound by the FP64 units and leaves most
+// of the memory bandwidth free, so the memory-bound pack and unpack kernels
+// and, with pinned host memory, the copies hide behind it.  Every copy is
 // one cudaMemcpyAsync of one contiguous field.
 #include <set>
 #include <string>
@@ -36,14 +38,15 @@ tm_status grow_stage(tm_ctx *ctx, size_t bytes)
     return TM_OK;
 }
 
-// The events of one call: per slot, "input copied", "input consumed by the
-// pack", "output unpacked", "output copied out".
+// The events of one call, per slot: "packed" (copy-in stream -> compute),
+// "multiplied" (compute -> both copy streams), "unpacked" (copy-out stream
+// -> compute).
 struct SlotEvents {
-    cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
+    cudaEvent_t packed[2] = {}, multiplied[2] = {}, unpacked[2] = {};
     cudaError_t create()
     {
         for (int k = 0; k < 2; ++k)
-            for (cudaEvent_t *e : {&in_ready[k], &in_free[k], &out_ready[k], &out_free[k]}) {
+            for (cudaEvent_t *e : {&packed[k], &multiplied[k], &unpacked[k]}) {
                 cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
                 if (r != cudaSuccess) return r;
             }
@@ -52,7 +55,7 @@ struct SlotEvents {
     ~SlotEvents()
     {
         for (int k = 0; k < 2; ++k)
-            for (cudaEvent_t e : {in_ready[k], in_free[k], out_ready[k], out_free[k]})
+            for (cudaEvent_t e : {packed[k], multiplied[k], unpacked[k]})
                 if (e) cudaEventDestroy(e);
     }
 };
@@ -102,22 +105,23 @@ extern "C" tm_status tm_Qtm_host(tm_ctx *ctx, const tm_gauge *U, int n, double *
     st = TM_OK;
     for (int k = 0; k < n && e == cudaSuccess && st == TM_OK; ++k) {
         const int q = k & 1;
-        // copy in, once the pack of field k-2 has consumed this slot
-        e = cudaStreamWaitEvent(ci, ev.in_free[q], 0);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(can_in[q], in_host[k], cb, cudaMemcpyHostToDevice, ci);
-        if (e == cudaSuccess) e = cudaEventRecord(ev.in_ready[q], ci);
-        // pack, operator, and (once field k-2 has left this slot) unpack
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.in_ready[q], 0);
-        if (e == cudaSuccess) e = launch_pack_spinor(vh, U->prec, can_in[q], p_in[q], s);
-        if (e == cudaSuccess) e = cudaEventRecord(ev.in_free[q], s);
+        // copy-in stream: field k to the device, then (once the operator of
+        // field k-2 has read this slot's packed input) its pack
+        e = cudaMemcpyAsync(can_in[q], in_host[k], cb, cudaMemcpyHostToDevice, ci);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, ev.multiplied[q], 0);
+        if (e == cudaSuccess) e = launch_pack_spinor(vh, U->prec, can_in[q], p_in[q], ci);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.packed[q], ci);
+        // compute stream: the operator, once field k is packed and the unpack
+        // of field k-2 has read this slot's packed output
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.packed[q], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.unpacked[q], 0);
         if (e == cudaSuccess) st = tm_Qtm(ctx, U, p_out[q], p_in[q], kappa, mu, sign, s);
-        if (e == cudaSuccess && st == TM_OK) e = cudaStreamWaitEvent(s, ev.out_free[q], 0);
-        if (e == cudaSuccess && st == TM_OK) e = launch_unpack_spinor(vh, U->prec, p_out[q], can_out[q], s);
-        if (e == cudaSuccess && st == TM_OK) e = cudaEventRecord(ev.out_ready[q], s);
-        // copy out
-        if (e == cudaSuccess && st == TM_OK) e = cudaStreamWaitEvent(co, ev.out_ready[q], 0);
+        if (e == cudaSuccess && st == TM_OK) e = cudaEventRecord(ev.multiplied[q], s);
+        // copy-out stream: unpack and copy field k back to the host
+        if (e == cudaSuccess && st == TM_OK) e = cudaStreamWaitEvent(co, ev.multiplied[q], 0);
+        if (e == cudaSuccess && st == TM_OK) e = launch_unpack_spinor(vh, U->prec, p_out[q], can_out[q], co);
+        if (e == cudaSuccess && st == TM_OK) e = cudaEventRecord(ev.unpacked[q], co);
         if (e == cudaSuccess && st == TM_OK) e = cudaMemcpyAsync(out_host[k], can_out[q], cb, cudaMemcpyDeviceToHost, co);
-        if (e == cudaSuccess && st == TM_OK) e = cudaEventRecord(ev.out_free[q], co);
     }
     // drain every stream before the events go away, whatever happened
     cudaError_t e1 = cudaStreamSynchronize(ci);
