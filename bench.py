@@ -56,9 +56,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # (profiles/k_hop_f64_24x24x24x48_full.md, profiles/k_hop_dram_f32_f16_32x32x32x64.md),
 # scaled to a 32^3x64 launch by the site count, valid only for the kernel
 # sources they were taken from (hash of csrc/tm_device.cuh + csrc/tm_kernels.cu).
-TRAFFIC = {"src": "904ec51bf61c8f7f",
-           "per_site": {("f64", 18): (512802560 + 35048448) / 331776, ("f64x", 18): (513013504 + 33841920) / 331776,
-                        ("f32", 12): (607451136 + 69692672) / 1048576, ("f16", 12): (312113152 + 28220928) / 1048576}}
+TRAFFIC = {"src": "c21978e1c0ace148",
+           "per_site": {("f64", 18): (512742400 + 35243264) / 331776, ("f64x", 18): (513207552 + 34457088) / 331776,
+                        ("f32", 12): (607362048 + 69624320) / 1048576, ("f16", 12): (312105984 + 28393984) / 1048576}}
 
 
 def kernel_source_hash() -> str:
