@@ -25,8 +25,8 @@ from paper_1311_4521_gb300 import fields as F
 
 pytestmark = pytest.mark.gpu
 
-TOLF = {"f64": 1e-12, "f64x": 1e-12, "f32": 1e-5}
-RECON = {"f64": 18, "f64x": 18, "f32": 12}
+TOLF = {"f64": 1e-12, "f64x": 1e-12, "f32": 1e-5, "f16": 5e-3}
+RECON = {"f64": 18, "f64x": 18, "f32": 12, "f16": 12}
 LAM = F._LAMBDA
 
 
@@ -48,7 +48,7 @@ def small():
     return dims, U, X
 
 
-@pytest.mark.parametrize("prec", ["f64", "f64x", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f64x", "f32", "f16"])
 def test_force_all_links_match_oracle(ctx, small, prec):
     from paper_1311_4521_gb300 import tmhop
     dims, U, X = small
