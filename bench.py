@@ -600,7 +600,9 @@ def batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U32=None) -> dict
     right-hand sides of one 32^3x64 lattice in one launch per hop, against 12
     single Q_tm calls; (b) CG to 1e-10 on the 12 right-hand sides and (c) on
     8 lattices of uneven volume (sum of V = 5,187,072 sites), each batch in
-    one call against the same systems solved one after the other."""
+    one call against the same systems solved one after the other; (d) Q_tm
+    on the 8 uneven lattices and (e) on 64 lattices of 8^4 in one call
+    against one call per lattice."""
     big = (32, 32, 32, 64)
     vh = int(np.prod(big)) // 2
     if U32 is None:
@@ -696,6 +698,25 @@ def batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U32=None) -> dict
                                    "speedup": round(te / tb, 2), "converged": st == tmhop.TM_OK,
                                    "iters": [i["iters"] for i in infos],
                                    "max_true_relres": max(i["true_relres"] for i in infos)}
+    # (d) Q_tm on the 8 uneven lattices in one call vs 8 calls, and (e) on 64
+    # small 8^4 lattices (an ensemble of small problems), FP32-12
+    def many_lattices(dims_list, seed0):
+        gs, ins_, outs_ = [], [], []
+        for k, d in enumerate(dims_list):
+            gs.append(ctx.gauge(d, F.gauge_field(d, seed0 + k, "near", 0.3), "f32", 12))
+            v = int(np.prod(d)) // 2
+            ins_.append(ctx.pack(F.gaussian_spinor(v, seed0 + k, 2), "f32"))
+            outs_.append(ctx.empty(v, "f32"))
+        r = max(3, min(50, args.steps // 20))
+        mb = timed(lambda: ctx.Qtm_batch(gs, outs_, ins_, KAPPA, MU), r)
+        ms = timed(lambda: [ctx.Qtm(g, o, i, KAPPA, MU) for g, o, i in zip(gs, outs_, ins_)], r)
+        for g in gs:
+            g.close()
+        return {"lattices": len(dims_list), "sites": int(sum(np.prod(d) for d in dims_list)),
+                "ms_batched": round(mb, 4), "ms_one_call_each": round(ms, 4), "speedup": round(ms / mb, 2)}
+
+    out["qtm_8_uneven_lattices"] = many_lattices(UNEVEN, F.SEED_BATCH_LATTICE)
+    out["qtm_64_lattices_8x8x8x8"] = many_lattices([(8, 8, 8, 8)] * 64, F.SEED_BATCH_LATTICE + 1000)
     for g in gh + gl:
         g.close()
     return out

@@ -274,8 +274,14 @@ tm_status tm_force_ex(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void 
  * gauge handle pointer are several right-hand sides of one lattice: the
  * links of each site are read once and applied to all of them.  Systems on
  * different handles may have different lattice sizes.  All handles must
- * have the same precision and reconstruction.  Scratch (odd temporaries)
- * is owned by ctx.  Synchronous with respect to stream. */
+ * have the same precision and reconstruction.  The batch's device tables
+ * and odd temporaries are owned by ctx.  Asynchronous on `stream` like
+ * tm_Qtm: the first call for a batch (its handles, field pointers, lattice
+ * sizes and stream) uploads its tables and, for a new batch shape, times
+ * launch configurations (both synchronise the stream); a repeated call with
+ * the same batch only launches.  Batched calls on one ctx that overlap on
+ * different streams are not supported (the ctx synchronises the previous
+ * stream when the stream changes). */
 tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U, void *const *out_e, const void *const *in_e,
                        double kappa, double mu, int sign, void *stream);
 

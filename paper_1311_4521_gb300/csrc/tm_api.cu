@@ -87,6 +87,7 @@ void tm_ctx_destroy(tm_ctx *ctx)
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->bq) cudaFree(ctx->bq);
     if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
     if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     delete ctx;

@@ -33,12 +33,25 @@
 
 namespace twm {
 
-// Maps a vector-kernel item to (system, tile of BLA sites) by the prefix table item0[nsys+1].
-__device__ __forceinline__ int find_sys(const unsigned *item0, int nsys, unsigned item)
+// Maps a vector-kernel item to (system, tile of BLA sites) by the prefix
+// table item0[nsys+1]; `staged` is its copy in shared memory (or null).
+__device__ __forceinline__ int find_sys(const unsigned *item0, const unsigned *staged, int nsys, unsigned item)
 {
+    if (staged) return find_first(staged, nsys, item);
     int k = 0;
     while (k + 1 < nsys && item >= item0[k + 1]) ++k;
     return k;
+}
+
+// Stages item0[0 .. nsys) in `buf` (shared memory of STAGE_MAX entries) when
+// it fits; every thread of the block must call it.  Returns the staged copy
+// or null.
+__device__ __forceinline__ const unsigned *stage_item0(const unsigned *item0, int nsys, unsigned *buf)
+{
+    if (nsys > STAGE_MAX) return nullptr;
+    for (int k = threadIdx.x; k < nsys; k += blockDim.x) buf[k] = item0[k];
+    __syncthreads();
+    return buf;
 }
 
 // Block sum of v over BLA threads in a fixed order (warp sums, then the
@@ -62,8 +75,10 @@ __global__ void __launch_bounds__(BLA, P == F64 ? 3 : 4) k_batch_pupdate(const B
                                                        unsigned nitems, int gate, int restart)
 {
     using R = typename SpinorIO<P>::R;
+    __shared__ unsigned item0_s[STAGE_MAX];
+    const unsigned *staged = stage_item0(item0, nsys, item0_s);
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int k = find_sys(item0, nsys, item);
+        const int k = find_sys(item0, staged, nsys, item);
         const BSys &S = sys[k];
         if (gated(S.s, gate)) continue;
         const unsigned i = (item - item0[k]) * BLA + threadIdx.x;
@@ -91,8 +106,10 @@ __global__ void __launch_bounds__(BLA, 4) k_batch_accum(const BSys *__restrict__
                                                      unsigned nitems, int gate)
 {
     using RY = typename SpinorIO<PY>::R;
+    __shared__ unsigned item0_s[STAGE_MAX];
+    const unsigned *staged = stage_item0(item0, nsys, item0_s);
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int k = find_sys(item0, nsys, item);
+        const int k = find_sys(item0, staged, nsys, item);
         const BSys &S = sys[k];
         if (gated(S.s, gate)) continue;
         const unsigned i = (item - item0[k]) * BLA + threadIdx.x;
@@ -121,8 +138,10 @@ __global__ void __launch_bounds__(BLA, 3) k_batch_residual(const BSys *__restric
 {
     using R = typename SpinorIO<P>::R;
     __shared__ double red[BLA / 32];
+    __shared__ unsigned item0_s[STAGE_MAX];
+    const unsigned *staged = stage_item0(item0, nsys, item0_s);
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int k = find_sys(item0, nsys, item);
+        const int k = find_sys(item0, staged, nsys, item);
         const BSys &S = sys[k];
         if (gated(S.s, gate)) continue;
         const unsigned tno = item - item0[k], i = tno * BLA + threadIdx.x;
@@ -153,8 +172,10 @@ __global__ void __launch_bounds__(BLA, 4) k_batch_norm(const BSys *__restrict__ 
                                                     unsigned nitems, int role)
 {
     __shared__ double red[BLA / 32];
+    __shared__ unsigned item0_s[STAGE_MAX];
+    const unsigned *staged = stage_item0(item0, nsys, item0_s);
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int k = find_sys(item0, nsys, item);
+        const int k = find_sys(item0, staged, nsys, item);
         const BSys &S = sys[k];
         const unsigned tno = item - item0[k], i = tno * BLA + threadIdx.x;
         double nrm = 0.0;
@@ -173,8 +194,10 @@ __global__ void __launch_bounds__(BLA, 4) k_batch_zero(const BSys *__restrict__ 
                                                     unsigned nitems, int role)
 {
     using R = typename SpinorIO<P>::R;
+    __shared__ unsigned item0_s[STAGE_MAX];
+    const unsigned *staged = stage_item0(item0, nsys, item0_s);
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int k = find_sys(item0, nsys, item);
+        const int k = find_sys(item0, staged, nsys, item);
         const BSys &S = sys[k];
         const unsigned i = (item - item0[k]) * BLA + threadIdx.x;
         if (i >= S.vh) continue;
@@ -391,45 +414,90 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     for (int k = 0; k < nsys; ++k) {
         if (bad_ptr(out_e[k]) || bad_ptr(in_e[k]) || out_e[k] == in_e[k]) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad field pointer");
     }
-    // workspace: odd temporaries, system table, group table
-    size_t need = 0;
-    for (int k = 0; k < nsys; ++k) need += align256(spinor_bytes(U[k]->geom.vh, prec));
-    need += align256(sizeof(BSys) * nsys) + align256(sizeof(BGroup) * handles.size());
-    void *base = nullptr;
-    st = tm_ctx_scratch(ctx, need, &base);
-    if (st != TM_OK) return st;
-    char *c = static_cast<char *>(base);
-    std::vector<BSys> hs;
-    std::vector<BGroup> tmpl;
-    std::vector<void *> tmp(nsys);
-    for (int k = 0; k < nsys; ++k) {
-        tmp[k] = c;
-        c += align256(spinor_bytes(U[k]->geom.vh, prec));
-    }
-    for (size_t g = 0; g < handles.size(); ++g) {
-        BGroup G{};
-        G.g = handles[g]->geom;
-        G.links = handles[g]->links;
-        G.nrhs = int(members[g].size());
-        G.sys0 = int(hs.size());
-        tmpl.push_back(G);
-        for (int k : members[g]) {
-            BSys S{};
-            S.f[R_IN] = const_cast<void *>(in_e[k]);
-            S.f[R_OUT] = out_e[k];
-            S.f[R_T] = tmp[k];
-            S.vh = U[k]->geom.vh;
-            hs.push_back(S);
-        }
-    }
-    BSys *dsys = reinterpret_cast<BSys *>(c);
-    c += align256(sizeof(BSys) * nsys);
-    BGroup *dgrp = reinterpret_cast<BGroup *>(c);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(dsys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
+    // The batch as the device tables describe it: handles (with their links
+    // and sizes), fields, precision and stream.  A repeated call with the same
+    // batch finds its tables and temporaries in place and only launches.
+    std::vector<uintptr_t> sig{uintptr_t(prec), uintptr_t(recon), uintptr_t(nsys), uintptr_t(s)};
+    for (int k = 0; k < nsys; ++k) {
+        sig.push_back(uintptr_t(U[k]));
+        sig.push_back(uintptr_t(U[k]->links));
+        const Geom &gk = U[k]->geom;   // a handle re-created at the same address may describe another lattice
+        sig.push_back((uintptr_t(gk.lx) << 48) | (uintptr_t(gk.ly) << 32) | (uintptr_t(gk.lz) << 16) | uintptr_t(gk.lt));
+        sig.push_back(uintptr_t(gk.anti[0]) | uintptr_t(gk.anti[1]) << 1 | uintptr_t(gk.anti[2]) << 2 |
+                      uintptr_t(gk.anti[3]) << 3);
+        sig.push_back(uintptr_t(out_e[k]));
+        sig.push_back(uintptr_t(in_e[k]));
+    }
     HopTable t;
-    if (e == cudaSuccess) e = tune_hop_table(ctx, prec, recon, tmpl, dgrp, dsys, R_IN, R_T, t, s);
-    if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: setup");
+    BSys *dsys = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (ctx->bq && sig == ctx->bq_sig) {
+        t.nrb = ctx->bq_tab.nrb;
+        t.grid = ctx->bq_tab.grid;
+        t.nitems = ctx->bq_tab.nitems;
+        t.ngroups = ctx->bq_tab.ngroups;
+        t.dev = static_cast<BGroup *>(ctx->bq_tab.dgrp);
+        dsys = static_cast<BSys *>(ctx->bq_tab.dsys);
+    } else {
+        // the previous batch's launches may still read the buffer on another stream
+        if (ctx->bq && ctx->bq_stream != s) {
+            e = cudaStreamSynchronize(ctx->bq_stream);
+            if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: previous batch");
+        }
+        ctx->bq_sig.clear();
+        // buffer: odd temporaries, system table, group table
+        size_t need = 0;
+        for (int k = 0; k < nsys; ++k) need += align256(spinor_bytes(U[k]->geom.vh, prec));
+        need += align256(sizeof(BSys) * nsys) + align256(sizeof(BGroup) * handles.size());
+        if (ctx->bq_bytes < need) {
+            if (ctx->bq) cudaFree(ctx->bq);
+            ctx->bq = nullptr;
+            ctx->bq_bytes = 0;
+            e = cudaMalloc(&ctx->bq, need);
+            if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: cudaMalloc");
+            ctx->bq_bytes = need;
+        }
+        char *c = static_cast<char *>(ctx->bq);
+        std::vector<BSys> hs;
+        std::vector<BGroup> tmpl;
+        std::vector<void *> tmp(nsys);
+        for (int k = 0; k < nsys; ++k) {
+            tmp[k] = c;
+            c += align256(spinor_bytes(U[k]->geom.vh, prec));
+        }
+        for (size_t g = 0; g < handles.size(); ++g) {
+            BGroup G{};
+            G.g = handles[g]->geom;
+            G.links = handles[g]->links;
+            G.nrhs = int(members[g].size());
+            G.sys0 = int(hs.size());
+            tmpl.push_back(G);
+            for (int k : members[g]) {
+                BSys S{};
+                S.f[R_IN] = const_cast<void *>(in_e[k]);
+                S.f[R_OUT] = out_e[k];
+                S.f[R_T] = tmp[k];
+                S.vh = U[k]->geom.vh;
+                hs.push_back(S);
+            }
+        }
+        dsys = reinterpret_cast<BSys *>(c);
+        c += align256(sizeof(BSys) * nsys);
+        BGroup *dgrp = reinterpret_cast<BGroup *>(c);
+        // pageable source: the copy has taken the data when the call returns
+        e = cudaMemcpyAsync(dsys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = tune_hop_table(ctx, prec, recon, tmpl, dgrp, dsys, R_IN, R_T, t, s);
+        if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: setup");
+        ctx->bq_sig = sig;
+        ctx->bq_stream = s;
+        ctx->bq_tab.nrb = t.nrb;
+        ctx->bq_tab.grid = t.grid;
+        ctx->bq_tab.nitems = t.nitems;
+        ctx->bq_tab.ngroups = t.ngroups;
+        ctx->bq_tab.dsys = dsys;
+        ctx->bq_tab.dgrp = dgrp;
+    }
     const double mut = 2.0 * kappa * mu * sign;
     tm_trace_mark(ctx, 0, s);
     e = bhop(prec, recon, t, dsys, 1, R_IN, R_T, -1, coef_qtm_a_scaled(kappa, mut), BH_PLAIN, 0, s);
@@ -437,9 +505,6 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     if (e == cudaSuccess) e = bhop(prec, recon, t, dsys, 0, R_T, R_OUT, R_IN, coef_qtm_b_unit(mut), BH_PLAIN, 0, s);
     tm_trace_mark(ctx, 2, s);
     if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: launch");
-    // the tables live in scratch: keep them until the launches have read them
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch");
     return TM_OK;
 }
 

@@ -41,8 +41,27 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-__device__ __forceinline__ int find_group(const BGroup *gr, int ng, unsigned item)
+// The first work item of every group (or system), staged once per CTA in
+// shared memory so that mapping an item to its group is a short binary
+// search there instead of a chain of dependent global loads.  Tables longer
+// than STAGE_MAX entries stay in global memory.
+constexpr int STAGE_MAX = 256;
+
+// Largest k < n with first[k] <= item (first[] strictly increasing, first[0] = 0).
+__device__ __forceinline__ int find_first(const unsigned *first, int n, unsigned item)
 {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_group(const BGroup *gr, int ng, const unsigned *staged, unsigned item)
+{
+    if (staged) return find_first(staged, ng, item);
     int gi = 0;
     while (gi + 1 < ng && item >= gr[gi + 1].item0) ++gi;
     return gi;
@@ -84,10 +103,16 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
     __shared__ V tile[NRB > 1 ? 8 * L::NCHUNK * TS : 1];
     __shared__ unsigned bwd_idx[NRB > 1 ? 4 * TS : 1];
     __shared__ double red[BT / 32];
+    __shared__ unsigned first[STAGE_MAX];
     const unsigned tx = threadIdx.x % TS, ty = threadIdx.x / TS;
+    const unsigned *staged = ngroups <= STAGE_MAX ? first : nullptr;
+    if (staged) {
+        for (int g = threadIdx.x; g < ngroups; g += BT) first[g] = groups[g].item0;
+        __syncthreads();
+    }
 
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const BGroup &G = groups[find_group(groups, ngroups, item)];
+        const BGroup &G = groups[find_group(groups, ngroups, staged, item)];
         const unsigned rel = item - G.item0;
         const unsigned tno = NRB <= 1 ? rel / unsigned(G.nrhs) : rel;
         const unsigned i = tno * TS + tx;

@@ -28,6 +28,17 @@ struct tm_ctx {
     size_t stage_bytes = 0;
     cudaStream_t copy_in = nullptr;  // copy streams of tm_Qtm_host (created on first use)
     cudaStream_t copy_out = nullptr;
+    // tm_Qtm_batch: its tables and odd temporaries (grow-only), and the batch
+    // they were built for, so that a repeated call only launches
+    void *bq = nullptr;
+    size_t bq_bytes = 0;
+    std::vector<uintptr_t> bq_sig;
+    cudaStream_t bq_stream = nullptr;
+    struct {
+        int nrb = 1, ngroups = 0;
+        unsigned grid = 0, nitems = 0;
+        void *dsys = nullptr, *dgrp = nullptr;
+    } bq_tab;
 };
 
 // Records msg as the context's last error (tm_last_error) and returns st.

@@ -68,6 +68,32 @@ def test_Qtm_batch_matches_oracle(ctx, prec, spec, autotune):
     tmhop.tm_ctx_set_autotune(ctx.handle, True)
 
 
+def test_Qtm_batch_repeated_and_rebuilt(ctx):
+    """A repeated batch reuses its device tables (new field contents, same
+    buffers); a different batch on another stream rebuilds them."""
+    import torch
+    dims = (8, 8, 8, 8)
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, 77, "random")
+    g = ctx.gauge(dims, U, "f32", 12)
+    ins = [ctx.pack(F.gaussian_spinor(vh, 77, 10 + j), "f32") for j in range(3)]
+    outs = [ctx.empty(vh, "f32") for _ in range(3)]
+    ctx.Qtm_batch([g] * 3, outs, ins, 0.1394, 0.0015)
+    psis = [F.gaussian_spinor(vh, 78, 10 + j) for j in range(3)]
+    for buf, psi in zip(ins, psis):
+        buf.copy_(ctx.pack(psi, "f32"))
+    ctx.Qtm_batch([g] * 3, outs, ins, 0.1394, 0.0015)
+    for out, psi in zip(outs, psis):
+        assert rel(ctx.unpack(out, vh, "f32").cpu().numpy(), O.Qtm(dims, U, psi, 0.1394, 0.0015)) < TOL["f32"]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ctx.Qtm_batch([g] * 2, outs[:2], ins[1:], 0.1394, 0.0015, -1)
+    torch.cuda.synchronize()
+    for out, psi in zip(outs[:2], psis[1:]):
+        assert rel(ctx.unpack(out, vh, "f32").cpu().numpy(), O.Qtm(dims, U, psi, 0.1394, -0.0015)) < TOL["f32"]
+    g.close()
+
+
 def oracle_relres(dims, U, x, b, kappa, mu):
     Ax = O.Qtm(dims, U, O.Qtm(dims, U, x, kappa, mu), kappa, -mu)
     return float(np.linalg.norm(b - Ax) / np.linalg.norm(b))
