@@ -274,7 +274,9 @@ tm_status tm_force_ex(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void 
  * gauge handle pointer are several right-hand sides of one lattice: the
  * links of each site are read once and applied to all of them.  Systems on
  * different handles may have different lattice sizes.  All handles must
- * have the same precision and reconstruction.  The batch's device tables
+ * have the same precision and reconstruction.  Every output buffer belongs
+ * to one system and is none of the inputs (TM_ERR_ARG); inputs may repeat.
+ * The batch's device tables
  * and odd temporaries are owned by ctx.  Asynchronous on `stream` like
  * tm_Qtm: the first call for a batch (its handles, field pointers, lattice
  * sizes and stream) uploads its tables and, for a new batch shape, times
@@ -292,9 +294,10 @@ tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U, void *co
  * solver); systems sharing U_hi need the same U_lo; all inner handles need
  * the same precision.  Every system uses the reliable-update scheme of
  * tm_cg_QdagQ with its own scalars and stops on its own FP64 true residual;
- * params are shared.  info[k] receives system k's statistics (seconds is
- * the batch's wall time).  Returns TM_OK if every system converged, else
- * TM_ERR_NONFINITE or TM_ERR_NOT_CONVERGED. */
+ * params are shared.  Every x[k] belongs to one system and is none of the
+ * b (TM_ERR_ARG); sources may repeat.  info[k] receives system k's
+ * statistics (seconds is the batch's wall time).  Returns TM_OK if every
+ * system converged, else TM_ERR_NONFINITE or TM_ERR_NOT_CONVERGED. */
 tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U_hi, const tm_gauge *const *U_lo,
                             void *const *x_dev, const void *const *b_dev, const tm_cg_params *params,
                             tm_cg_info *info, void *stream);

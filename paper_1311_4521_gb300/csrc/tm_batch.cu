@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -414,6 +415,12 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     for (int k = 0; k < nsys; ++k) {
         if (bad_ptr(out_e[k]) || bad_ptr(in_e[k]) || out_e[k] == in_e[k]) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: bad field pointer");
     }
+    {   // every output is written by one system and read by none (inputs may repeat)
+        std::set<const void *> outs(out_e, out_e + nsys), ins(in_e, in_e + nsys);
+        if (int(outs.size()) != nsys) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: an output field appears twice");
+        for (const void *o : outs)
+            if (ins.count(o)) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: an output field is also an input");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     // The batch as the device tables describe it: handles (with their links
     // and sizes), fields, precision and stream.  A repeated call with the same
@@ -533,6 +540,12 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
                 return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: U_hi and U_lo describe different lattices");
             if (bad_ptr(x_dev[k]) || bad_ptr(b_dev[k]) || x_dev[k] == b_dev[k]) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: bad field pointer");
         }
+    }
+    {   // every solution is written by one system and read by none (sources may repeat)
+        std::set<const void *> xs(x_dev, x_dev + nsys), bs(b_dev, b_dev + nsys);
+        if (int(xs.size()) != nsys) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: a solution field appears twice");
+        for (const void *x : xs)
+            if (bs.count(x)) return tm_fail(ctx, TM_ERR_ARG, "tm_cg_QdagQ_batch: a solution field is also a source");
     }
     for (size_t g = 0; g < handles.size(); ++g)
         if (lo[g]->prec != lo[0]->prec || lo[g]->recon != lo[0]->recon || handles[g]->recon != handles[0]->recon)

@@ -94,6 +94,21 @@ def test_Qtm_batch_repeated_and_rebuilt(ctx):
     g.close()
 
 
+def test_Qtm_batch_argument_errors(ctx):
+    from paper_1311_4521_gb300 import tmhop
+    dims = (4, 4, 4, 4)
+    g = ctx.gauge(dims, F.gauge_field(dims, 5, "random"), "f32", 12)
+    a, b, c = (ctx.empty(128, "f32") for _ in range(3))
+    with pytest.raises(tmhop.TmError) as e:
+        ctx.Qtm_batch([g, g], [a, a], [b, c], 0.1, 0.1)     # one output for two systems
+    assert e.value.status == tmhop.TM_ERR_ARG
+    with pytest.raises(tmhop.TmError) as e:
+        ctx.Qtm_batch([g, g], [a, b], [b, c], 0.1, 0.1)     # an output read by another system
+    assert e.value.status == tmhop.TM_ERR_ARG
+    ctx.Qtm_batch([g, g], [a, b], [c, c], 0.1, 0.1)         # a repeated input is fine
+    g.close()
+
+
 def oracle_relres(dims, U, x, b, kappa, mu):
     Ax = O.Qtm(dims, U, O.Qtm(dims, U, x, kappa, mu), kappa, -mu)
     return float(np.linalg.norm(b - Ax) / np.linalg.norm(b))
@@ -143,6 +158,12 @@ def test_cg_batch_argument_errors(ctx):
         ctx.cg_batch([g64, g64b], [x, x2], [b, b], 0.1, 0.01, U_lo=[g32, g16])
     with pytest.raises(tmhop.TmError):   # FP32 as U_hi
         ctx.cg_batch([g32], [x], [b], 0.1, 0.01)
+    with pytest.raises(tmhop.TmError) as e:   # one solution field for two systems
+        ctx.cg_batch([g64, g64], [x, x], [b, b], 0.1, 0.01)
+    assert e.value.status == tmhop.TM_ERR_ARG
+    with pytest.raises(tmhop.TmError) as e:   # a solution that is another system's source
+        ctx.cg_batch([g64, g64], [x, x2], [b, x], 0.1, 0.01)
+    assert e.value.status == tmhop.TM_ERR_ARG
 
 
 def test_batching_workload_full_size(ctx):
