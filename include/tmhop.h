@@ -236,8 +236,9 @@ tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_
  * out_host[k] = Q in_host[k], each a complex double [Vh][4][3] array (the
  * layout tm_spinor_pack reads).  The fields go through two device staging
  * slots in U's storage precision, pipelined: field k+1 is copied to the
- * device and field k-1 back to the host on two copy streams owned by the
- * context while field k is packed, multiplied and unpacked on `stream`.
+ * device and packed on one copy stream owned by the context, field k-1
+ * unpacked and copied back on the other, while field k is multiplied on
+ * `stream`.
  * Host buffers should be pinned (cudaHostAlloc, cudaHostRegister) for the
  * copies to overlap the kernels; pageable memory works but serialises.  No
  * output may be one of the inputs (TM_ERR_ARG), and no buffers may overlap.
