@@ -38,33 +38,37 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(lib):
+    """Declares the argument and result types of the library's functions."""
+    P = ctypes.c_void_p
+    I4 = ctypes.POINTER(ctypes.c_int)
+    D = ctypes.c_double
+    L = ctypes.c_long
+    lib.oracle_check_dims.argtypes = [I4]
+    lib.oracle_check_dims.restype = ctypes.c_int
+    lib.oracle_gammas.argtypes = [P]
+    lib.oracle_dhop.argtypes = [I4, I4, P, P, P, ctypes.c_int]
+    lib.oracle_dhop_dagger.argtypes = [I4, I4, P, P, P, ctypes.c_int]
+    lib.oracle_pack_eo.argtypes = [I4, ctypes.c_int, P, P]
+    lib.oracle_unpack_eo.argtypes = [I4, ctypes.c_int, P, P]
+    lib.oracle_hopping.argtypes = [I4, I4, P, ctypes.c_int, P, P, ctypes.c_int]
+    lib.oracle_gamma5.argtypes = [L, P, P]
+    lib.oracle_twist.argtypes = [L, D, P, P]
+    lib.oracle_twist_inv.argtypes = [L, D, P, P]
+    lib.oracle_Qtm.argtypes = [I4, I4, P, D, D, P, P]
+    lib.oracle_Qtm_dagger.argtypes = [I4, I4, P, D, D, P, P]
+    lib.oracle_cg_QdagQ.argtypes = [I4, I4, P, D, D, P, P, D, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(D)]
+    lib.oracle_cg_QdagQ.restype = ctypes.c_int
+    lib.oracle_force.argtypes = [I4, I4, P, D, D, P, ctypes.c_int, P, P]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            I4 = ctypes.POINTER(ctypes.c_int)
-            D = ctypes.c_double
-            L = ctypes.c_long
-            lib.oracle_check_dims.argtypes = [I4]
-            lib.oracle_check_dims.restype = ctypes.c_int
-            lib.oracle_gammas.argtypes = [P]
-            lib.oracle_dhop.argtypes = [I4, I4, P, P, P, ctypes.c_int]
-            lib.oracle_dhop_dagger.argtypes = [I4, I4, P, P, P, ctypes.c_int]
-            lib.oracle_pack_eo.argtypes = [I4, ctypes.c_int, P, P]
-            lib.oracle_unpack_eo.argtypes = [I4, ctypes.c_int, P, P]
-            lib.oracle_hopping.argtypes = [I4, I4, P, ctypes.c_int, P, P, ctypes.c_int]
-            lib.oracle_gamma5.argtypes = [L, P, P]
-            lib.oracle_twist.argtypes = [L, D, P, P]
-            lib.oracle_twist_inv.argtypes = [L, D, P, P]
-            lib.oracle_Qtm.argtypes = [I4, I4, P, D, D, P, P]
-            lib.oracle_Qtm_dagger.argtypes = [I4, I4, P, D, D, P, P]
-            lib.oracle_cg_QdagQ.argtypes = [I4, I4, P, D, D, P, P, D, ctypes.c_int,
-                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(D)]
-            lib.oracle_cg_QdagQ.restype = ctypes.c_int
-            lib.oracle_force.argtypes = [I4, I4, P, D, D, P, ctypes.c_int, P, P]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
 
 
