@@ -48,14 +48,19 @@ L2_BYTES = 129 * 2 ** 20
 REAL = {"f64": 8, "f64x": 8, "f32": 4, "f16": 2}
 HOP_FLOPS = 1320
 QTM_FLOPS = 2 * HOP_FLOPS + 72 + 96
-# FP64 ALU peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_FMA_PER_SM_CLK = 2     # nominal FP64 FMA lanes per SM and clock of a GB300 (context beside the probe)
 
 
-# DRAM bytes (read + write) per launch of Q_tm's launch B from ncu captures
-# (profiles/k_hop_f64_24x24x24x48_full.md, profiles/k_hop_dram_f32_f16_32x32x32x64.md),
-# scaled to a 32^3x64 launch by the site count, valid only for the kernel
-# sources they were taken from (hash of csrc/tm_device.cuh + csrc/tm_kernels.cu).
+def fp64_nominal_tflops(sm_count: int, sm_mhz: float) -> float:
+    """Nominal FP64 FMA rate: SMs x FMA lanes x 2 flop x clock."""
+    return sm_count * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+
+
+# DRAM bytes (read + write) per launch of Q_tm's launch B from ncu captures of
+# the dominant kernel (FP64 and double-float on 24^3x48, FP32/FP16 on
+# 32^3x64), scaled to a full launch by the site count, valid only for the
+# kernel sources they were taken from (hash of csrc/tm_device.cuh +
+# csrc/tm_kernels.cu).
 TRAFFIC = {"src": "c21978e1c0ace148",
            "per_site": {("f64", 18): (512742400 + 35243264) / 331776, ("f64x", 18): (513207552 + 34457088) / 331776,
                         ("f32", 12): (607362048 + 69624320) / 1048576, ("f16", 12): (312105984 + 28393984) / 1048576}}
@@ -257,6 +262,23 @@ def gpu_arm(args) -> None:
             dist.destroy_process_group()
         return
 
+    # ---- the FP64 arithmetic peak, measured on this GPU in this process
+    # (FMA throughput probe of the library) with the clocks it ran at
+    sms = props.multi_processor_count
+    pclk = ClockSampler(uuid).start()
+    f64s, t_probe = [], time.perf_counter()
+    while time.perf_counter() - t_probe < 1.0 or len(f64s) < 3:   # ~1 s, so that the clocks get sampled
+        f64s.append(tmhop.tm_probe_fma(ctx.handle, tmhop.TM_F64))
+    fp64_peak = max(f64s)
+    fp32_peak = tmhop.tm_probe_fma(ctx.handle, tmhop.TM_F32)
+    pck = pclk.stop()
+    probe = {"fp64_tflops": round(fp64_peak, 4), "fp64_tflops_median": round(statistics.median(f64s), 4),
+             "probe_calls": len(f64s), "fp32_tflops": round(fp32_peak, 2), "sm_count": sms,
+             "sm_mhz": pck.get("sm_mhz"), "reasons": pck.get("reasons"),
+             "fp64_nominal_tflops_at_max_clock": round(fp64_nominal_tflops(sms, pck.get("sm_max_mhz") or 2070.0), 4),
+             "how": "tm_probe_fma: 8 CTAs x 256 threads per SM, 8 independent FMA chains per thread, "
+                    "best of 3 timed launches of ~10 ms, 2 flop per FMA"}
+
     # ---- headline: FP64 storage, 18-real links (by default)
     g = ctx.gauge(DIMS, U, prec, recon)
     src = ctx.pack(psi, prec)
@@ -280,10 +302,12 @@ def gpu_arm(args) -> None:
     traffic = args.traffic if args.traffic is not None else traffic_per_launch(prec, recon, vh)
     kname = f"k_hop<{prec.upper()},{recon},HASX> (Q_tm second launch: H_eo + gamma5 twisted update)"
     if prec == "f64":
-        roofline = {"bound": "alu", "achieved": round(kb_tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                    "unit": "TFLOP/s", "frac": round(kb_tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+        roofline = {"bound": "alu", "achieved": round(kb_tflops, 4), "peak": round(fp64_peak, 4),
+                    "unit": "TFLOP/s", "frac": round(kb_tflops / fp64_peak, 4), "traffic": traffic,
                     "kernel": kname,
-                    "peak_source": "FP64 FMA units: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.257)",
+                    "peak_source": "measured: FP64 FMA throughput probe (tm_probe_fma) in this process, "
+                                   "see fp64_probe",
+                    "peak_nominal": probe["fp64_nominal_tflops_at_max_clock"],
                     "hbm_achieved_gbs": round(kb_gbs, 1), "hbm_frac": round(kb_gbs / hbm_peak, 4)}
     else:
         roofline = {"bound": "hbm", "achieved": round(kb_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
@@ -421,7 +445,8 @@ def gpu_arm(args) -> None:
             "config": dict(workload_config(DIMS, prec, recon, world),
                            l2=f"inputs larger than L2 ({links_gb:.2f} GB links "
                               f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"),
-            "gflops": round(gflops, 2), "roofline": roofline, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+            "gflops": round(gflops, 2), "roofline": roofline, "fp64_probe": probe, "hbm_peak_gbs": hbm_peak,
+            "hbm_peak_source": hbm_src,
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
             "cpu_baseline": cpu,
         }

@@ -241,7 +241,10 @@ tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_
  * `stream`.
  * Host buffers should be pinned (cudaHostAlloc, cudaHostRegister) for the
  * copies to overlap the kernels; pageable memory works but serialises.  No
- * output may be one of the inputs (TM_ERR_ARG), and no buffers may overlap.
+ * output may be one of the inputs or overlap one (an output that is an input
+ * gives TM_ERR_ARG).  Inputs may repeat, and so may outputs: the results are
+ * copied back in field order on one stream, so an output buffer given for
+ * several fields ends up holding the result of the last of them.
  * Synchronous: returns when every output is in host memory.  Device memory:
  * two slots of two canonical and two packed fields, kept by the context
  * (grow-only), plus tm_Qtm's scratch.  The paper has no counterpart; this is
@@ -303,6 +306,42 @@ tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U_hi, 
                             void *const *x_dev, const void *const *b_dev, const tm_cg_params *params,
                             tm_cg_info *info, void *stream);
 
+/* ---- measurement and field utilities -------------------------------------- */
+
+/* Measures the fused multiply-add throughput of the device in precision prec
+ * (TM_F64 or TM_F32): 8 CTAs of 256 threads per SM, each thread running 8
+ * independent FMA chains for about 10 ms; the best of three timed launches
+ * (CUDA events on `stream`, after one warm-up launch) at 2 flop per FMA is
+ * written to *tflops (host memory) in TFLOP/s.  It is the arithmetic peak the
+ * FP64 operator, which on this GPU is bound by its FP64 units rather than by
+ * memory, is measured against.  The paper has no counterpart (its machines
+ * were measured against their own nominal peaks).  Synchronous; allocates
+ * nothing. */
+tm_status tm_probe_fma(tm_ctx *ctx, int prec, double *tflops, void *stream);
+
+/* out_dev[0] + i out_dev[1] = <a, b> = sum over the Vh sites and 12
+ * spin-colour components of conj(a) b, for two packed one-parity fields of
+ * precision prec, accumulated in FP64 (the global inner product of the
+ * paper's Sec. 3, "scalar_prod_r", on one GPU).  The summation order depends
+ * only on Vh and the device's SM count, so repeated calls give identical
+ * bits.  out_dev is device memory holding two doubles, 8-byte aligned.
+ * Asynchronous on `stream`; the partial sums live in a buffer owned by ctx
+ * (grow-only), so calls on one ctx must not overlap on different streams. */
+tm_status tm_spinor_dot(tm_ctx *ctx, long vh, const void *a_dev, const void *b_dev, int prec, double *out_dev,
+                        void *stream);
+
+/* z[k] <- c * alpha * z[k] for the n complex doubles at z_dev (re, im
+ * interleaved, 16-byte aligned), with alpha = *alpha_dev read on the device
+ * (a scalar the caller keeps in device memory, e.g. an upstream gradient) or
+ * alpha = 1 when alpha_dev is NULL.  Asynchronous on `stream`. */
+tm_status tm_scale_complex(tm_ctx *ctx, size_t n, double *z_dev, const double *alpha_dev, double c, void *stream);
+
+/* Bytes of device memory the context holds at this moment (its scratch,
+ * solver workspace, staging slots, batch tables and reduction buffer; gauge
+ * handles are counted by tm_gauge_bytes).  0 for a context that has not yet
+ * allocated anything. */
+size_t tm_ctx_device_bytes(const tm_ctx *ctx);
+
 /* Size in bytes of the static device array behind tm_Qtm_noalloc: room for
  * one odd-parity field of up to 174,762 sites in TM_F64 (e.g. 24^3x24),
  * 349,525 in TM_F32 (24^3x48) or 645,277 in TM_F16 (32^3x32 and below).
@@ -321,9 +360,13 @@ tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U_hi, 
  * (tm_spinor_bytes(V/2, prec)) exceeds the array are rejected with
  * TM_ERR_ARG.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, with that device made current for the
- * lookup); make that first call before any stream capture.  All calls on a
- * device share the one array, which keeps the last call's contents; calls
- * that overlap on the GPU race on it. */
+ * lookup) and caches it for the life of the process; make that first call
+ * before any stream capture.  The cached address belongs to the device's
+ * primary context: after a cudaDeviceReset every object of this library
+ * (contexts, gauge handles, and this address) is invalid and must not be
+ * used again.  All calls on a device share the one array, which keeps the
+ * last call's contents; calls that overlap on the GPU race on it.  With
+ * tm_ctx_trace on, records the same three events as tm_Qtm. */
 tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in_e_dev, double kappa,
                          double mu, int sign, void *stream);
 

@@ -9,7 +9,14 @@ operators (the daggered hop, Q(-mu) = Q^dag) and tm_force.
 
 Gradients follow PyTorch's convention for a real loss of complex inputs,
 grad = dL/dRe z + i dL/dIm z: for S, dS/dphi = 2 X with X = (Q^dag Q)^-1 phi,
-and dS/dU = 2 kappa^2 s (M1^dag + M2) per link (see tm_force).
+and dS/dU = 2 kappa^2 s (M1^dag + M2) per link (see tm_force).  The action
+value, the scaling of the spinor gradient and of the link gradient by the
+upstream gradient are library calls too (tm_spinor_dot, tm_scale_complex):
+this module only moves buffers between torch and the library.
+
+HoppingEO and Qtm are differentiable in the spinor only; asking for their
+gradient with respect to the links raises NotImplementedError (the link
+gradient is provided for the action S, through tm_force).
 """
 from __future__ import annotations
 
@@ -68,6 +75,9 @@ class HoppingEO(torch.autograd.Function):
 
     @staticmethod
     def backward(fctx, grad):
+        if fctx.needs_input_grad[1]:
+            raise NotImplementedError("HoppingEO: the gradient with respect to the links is not provided "
+                                      "(the link gradient exists for the action S, see Action)")
         (U,) = fctx.saved_tensors
         dims, direction, prec, bc = fctx.cfg
         ctx = context(grad.device.index)
@@ -101,6 +111,9 @@ class Qtm(torch.autograd.Function):
 
     @staticmethod
     def backward(fctx, grad):
+        if fctx.needs_input_grad[1]:
+            raise NotImplementedError("Qtm: the gradient with respect to the links is not provided "
+                                      "(the link gradient exists for the action S, see Action)")
         (U,) = fctx.saved_tensors
         dims, kappa, mu, prec, bc = fctx.cfg
         ctx = context(grad.device.index)
@@ -138,7 +151,9 @@ class Action(torch.autograd.Function):
         if st != tmhop.TM_OK:
             raise tmhop.TmError(st, f"Action: solver failed: {info}")
         X = ctx.unpack(x, vh, "f64")
-        S = torch.real(torch.vdot(phi.detach().reshape(-1), X.reshape(-1)))
+        dot = torch.empty(2, dtype=torch.float64, device=x.device)
+        tmhop.tm_spinor_dot(ctx.handle, vh, b, x, tmhop.TM_F64, dot)   # <phi, X>, real up to rounding
+        S = dot[0].clone()
         fctx.save_for_backward(U, X)
         fctx.cfg = (dims, kappa, mu, force_prec, bc)
         return S
@@ -148,14 +163,16 @@ class Action(torch.autograd.Function):
         U, X = fctx.saved_tensors
         dims, kappa, mu, force_prec, bc = fctx.cfg
         grad_phi = grad_U = None
+        ctx = context(X.device.index)
+        gS = gS.detach().to(device=X.device, dtype=torch.float64).contiguous()
         if fctx.needs_input_grad[0]:
-            grad_phi = 2.0 * X * gS
+            grad_phi = X.clone()      # dS/dphi = 2 X, times the upstream gradient
+            tmhop.tm_scale_complex(ctx.handle, grad_phi.numel(), torch.view_as_real(grad_phi), gS, 2.0)
         if fctx.needs_input_grad[1]:
-            ctx = context(X.device.index)
             g = _gauge(ctx, dims, U, force_prec, bc)
-            G = ctx.force(g, ctx.pack(X, force_prec), kappa, mu, tmhop.TM_FORCE_GRAD)
+            grad_U = ctx.force(g, ctx.pack(X, force_prec), kappa, mu, tmhop.TM_FORCE_GRAD)
             g.close()
-            grad_U = G * gS
+            tmhop.tm_scale_complex(ctx.handle, grad_U.numel(), torch.view_as_real(grad_U), gS, 1.0)
         return grad_phi, grad_U, None, None, None, None, None, None, None
 
 
@@ -169,13 +186,3 @@ def qtm(psi, U, dims, kappa, mu, prec="f64", bc=(-1, 1, 1, 1)):
 
 def action(phi, U, dims, kappa, mu, tol=1e-10, inner="f64", force_prec="f64", bc=(-1, 1, 1, 1)):
     return Action.apply(phi, U, tuple(dims), float(kappa), float(mu), float(tol), inner, force_prec, tuple(bc))
-
-
-def su3_force(U: torch.Tensor, grad_U: torch.Tensor) -> torch.Tensor:
-    """The su(3) force F = -TA(U G^dag)/2 from the complex gradient G = dS/dU:
-    U -> exp(eps T) U changes S by eps <T, F> with <A,B> = -2 tr(AB)."""
-    W = U @ grad_U.conj().transpose(-1, -2)
-    A = 0.5 * (W - W.conj().transpose(-1, -2))
-    tr = torch.diagonal(A, dim1=-2, dim2=-1).sum(-1) / 3
-    eye = torch.eye(3, dtype=A.dtype, device=A.device)
-    return -0.5 * (A - tr[..., None, None] * eye)

@@ -51,6 +51,22 @@ tm_status tm_ctx_scratch(tm_ctx *ctx, size_t bytes, void **ptr)
     return TM_OK;
 }
 
+tm_status tm_ctx_reduce_buffer(tm_ctx *ctx, size_t bytes, void **ptr)
+{
+    if (ctx->red_bytes < bytes) {
+        if (ctx->red) {
+            cudaError_t e = cudaFree(ctx->red);
+            ctx->red = nullptr;
+            ctx->red_bytes = 0;
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree(reduce buffer)");
+        }
+        TM_CUDA(ctx, cudaMalloc(&ctx->red, bytes));
+        ctx->red_bytes = bytes;
+    }
+    *ptr = ctx->red;
+    return TM_OK;
+}
+
 extern "C" {
 
 const char *tm_status_string(tm_status s)
@@ -88,6 +104,7 @@ void tm_ctx_destroy(tm_ctx *ctx)
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->bq) cudaFree(ctx->bq);
+    if (ctx->red) cudaFree(ctx->red);
     if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
     if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     delete ctx;

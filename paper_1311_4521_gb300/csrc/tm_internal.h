@@ -21,6 +21,8 @@ struct tm_ctx {
     std::vector<cudaEvent_t> trace;  // events recorded at kernel boundaries (tm_ctx_trace)
     void *ws = nullptr;              // solver workspace (grow-only)
     size_t ws_bytes = 0;
+    void *red = nullptr;             // partial sums of tm_spinor_dot (grow-only)
+    size_t red_bytes = 0;
     int autotune = 1;                // time launch configurations on first use
     std::map<std::string, std::pair<int, unsigned>> tuned;  // batched hop: key -> (pass width, CTA cap)
     std::map<std::string, float> tuned_ms;                  // and the winner's time for 3 launches
@@ -81,6 +83,8 @@ inline double reliable_delta_for(double delta, int inner_prec)
 tm_status tm_ctx_scratch(tm_ctx *ctx, size_t bytes, void **ptr);
 // Grows the context's solver workspace to at least `bytes` and returns it.
 tm_status tm_ctx_workspace(tm_ctx *ctx, size_t bytes, void **ptr);
+// Grows the context's reduction buffer (partials of tm_spinor_dot) and returns it.
+tm_status tm_ctx_reduce_buffer(tm_ctx *ctx, size_t bytes, void **ptr);
 
 struct tm_gauge {
     tm_ctx *ctx = nullptr;

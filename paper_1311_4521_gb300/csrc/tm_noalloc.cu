@@ -36,7 +36,11 @@ void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_qtm_scratch on the context's device, looked up once
 // per device with that device current (the caller's current device is
-// restored afterwards).
+// restored afterwards) and kept for the life of the process.  It belongs to
+// the device's primary context: a cudaDeviceReset destroys that context and
+// with it every allocation of this library (contexts' buffers, gauge
+// handles), so after a reset the library is not used again on that device
+// and the stale address is never read.
 tm_status scratch_address(tm_ctx *ctx, void **addr)
 {
     if (ctx->device < 0 || ctx->device >= kMaxDevices)
@@ -84,11 +88,15 @@ extern "C" tm_status tm_Qtm_noalloc(tm_ctx *ctx, const tm_gauge *U, void *out_e_
     if (st != TM_OK) return st;
     double mut = 2.0 * kappa * mu * sign;
     cudaStream_t s = (cudaStream_t)stream;
+    tm_trace_mark(ctx, 0, s);
     cudaError_t e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, in_e_dev, tmp, nullptr,
                                coef_qtm_a_scaled(kappa, mut), s, 128);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+        tm_trace_mark(ctx, 1, s);
         e = launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, tmp, out_e_dev, in_e_dev,
                        coef_qtm_b_unit(mut), s, 128);
+    }
+    if (e == cudaSuccess) tm_trace_mark(ctx, 2, s);
     if (e != cudaSuccess)
         return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_Qtm_noalloc: launch: ") + cudaGetErrorString(e));
     return TM_OK;

@@ -80,6 +80,10 @@ def _load() -> ctypes.CDLL:
         "tm_Qtm_batch": ([P, I, P, P, P, D, D, I, P], I),
         "tm_Qtm_host": ([P, P, I, P, P, D, D, I, P], I),
         "tm_cg_QdagQ_batch": ([P, I, P, P, P, P, ctypes.POINTER(CgParams), P, P], I),
+        "tm_probe_fma": ([P, I, ctypes.POINTER(D), P], I),
+        "tm_spinor_dot": ([P, L, P, P, I, P, P], I),
+        "tm_scale_complex": ([P, S, P, P, D, P], I),
+        "tm_ctx_device_bytes": ([P], S),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -262,6 +266,29 @@ def tm_Qtm_noalloc(ctx, U, out_e_dev, in_e_dev, kappa, mu, sign=1, stream=None):
 
 
 TM_QTM_NOALLOC_MAX_BYTES = 32 << 20
+
+
+def tm_probe_fma(ctx, prec=TM_F64, stream=None) -> float:
+    """Measured FMA throughput of the device in TFLOP/s (prec TM_F64 or TM_F32).  Synchronous."""
+    out = ctypes.c_double()
+    _check(ctx, lib.tm_probe_fma(ctx, int(prec), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def tm_spinor_dot(ctx, vh, a_dev, b_dev, prec, out_dev, stream=None):
+    """out_dev (two device doubles) = <a, b> of two packed fields, FP64, fixed summation order."""
+    _check(ctx, lib.tm_spinor_dot(ctx, int(vh), _ptr(a_dev), _ptr(b_dev), int(prec), _ptr(out_dev),
+                                  _stream(stream)))
+
+
+def tm_scale_complex(ctx, n, z_dev, alpha_dev, c, stream=None):
+    """z <- c * alpha * z for n complex doubles in device memory (alpha_dev: device double or None)."""
+    _check(ctx, lib.tm_scale_complex(ctx, int(n), _ptr(z_dev), _ptr(alpha_dev), float(c), _stream(stream)))
+
+
+def tm_ctx_device_bytes(ctx) -> int:
+    """Bytes of device memory the context holds (not counting gauge handles)."""
+    return int(lib.tm_ctx_device_bytes(ctx))
 
 
 # ---- convenience layer over torch tensors -----------------------------------------

@@ -22,6 +22,7 @@ import torch
 
 import oracle as O
 from paper_1311_4521_gb300 import fields as F
+from su3_util import su3_force
 
 pytestmark = pytest.mark.gpu
 
@@ -71,8 +72,7 @@ def test_gradient_mode_gives_the_force(ctx, small):
     G = ctx.force(g, xp, 0.16, 0.01, tmhop.TM_FORCE_GRAD)
     Fs = ctx.force(g, xp, 0.16, 0.01, tmhop.TM_FORCE_SU3)
     g.close()
-    Ud = torch.from_numpy(U).to(G.device)
-    assert rel(autograd.su3_force(Ud, G).cpu().numpy(), Fs.cpu().numpy()) < 1e-13
+    assert rel(su3_force(U, G.cpu().numpy()), Fs.cpu().numpy()) < 1e-13
 
 
 SCHEMES = ("atomic", "halo")
@@ -101,9 +101,7 @@ def test_push_schemes_match_oracle(ctx, small, prec, mode):
     if mode == 0:
         assert rel(got["halo"], want) < TOLF[prec]
     else:
-        from paper_1311_4521_gb300 import autograd
-        Ud = torch.from_numpy(U)
-        Fs = autograd.su3_force(Ud, torch.from_numpy(got["halo"])).numpy()
+        Fs = su3_force(U, got["halo"])
         assert rel(Fs, want) < TOLF[prec]
 
 
@@ -275,7 +273,7 @@ def test_autograd_action_gradients(ctx):
     # dS/dU -> su(3) force against the oracle force for the solver's X
     X, _, _, ok = O.cg_QdagQ(dims, U, phi, k, mu, tol=1e-13, maxiter=10000)
     Fo = O.force(dims, U, X, k, mu)
-    Fa = autograd.su3_force(Ut.detach(), gU).cpu().numpy()
+    Fa = su3_force(U, gU.cpu().numpy())
     assert rel(Fa, Fo) < 1e-9
 
 

@@ -38,8 +38,15 @@ def test_two_rank_aggregation():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
+    try:
+        for p in procs:
+            p.join(timeout=120)
+    finally:
+        for p in procs:          # a hung rank must not outlive the test
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=10)
     for p in procs:
-        p.join(timeout=120)
         assert p.exitcode == 0
     out = sorted(q.get(timeout=10) for _ in range(2))
     for _, t_max, value in out:
