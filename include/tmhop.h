@@ -306,6 +306,60 @@ tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U_hi, 
                             void *const *x_dev, const void *const *b_dev, const tm_cg_params *params,
                             tm_cg_info *info, void *stream);
 
+/* ---- slabs: the operator on a lattice cut along time, one slab per GPU ------ */
+
+/* The paper's Sec. 2.5 splits the hopping matrix of a lattice distributed
+ * over MPI processes into the "surface" (sites whose neighbours live on
+ * another process) and the "body", sends the projected half-spinors of the
+ * surface and overlaps that communication with the body loop.  Here a
+ * lattice Lx x Ly x Lz x Lt is cut along t into slabs of even extent Lt_s >= 2
+ * (each starting at an even global t, so local and global parities agree),
+ * one per GPU.  A slab is an ordinary local lattice: its gauge handle is made
+ * by tm_gauge_create from the slab's own links U[4][Vs][3][3] (including U_0
+ * of its top time slice, which points into the next slab); its fields are
+ * packed one-parity fields of the slab.  Only the hops across the slab's two
+ * time faces need data from the neighbouring slabs, 12 reals per face site:
+ *   lower face (t = 0) of the INPUT field, sent to the previous slab:
+ *       the upper pair of (1 -+ gamma_0) psi, for that slab's forward hops;
+ *   upper face (t = Lt_s-1), sent to the next slab: U_0^dag times the upper
+ *       pair of (1 +- gamma_0) psi, for that slab's backward hops.
+ * A face holds the (Lx Ly Lz / 2) sites of one time slice and parity,
+ * component-major in FP64 (TM_F64 handles) or FP32 (TM_F32, TM_F16), and
+ * occupies tm_slab_face_bytes(U) bytes.  Supported storage: TM_F64, TM_F32,
+ * TM_F16 (TM_F64X gives 0 / TM_ERR_UNSUPPORTED). */
+enum { TM_SLAB_INTERIOR = 1,   /* output sites with 1 <= t <= Lt_s-2 (no face data needed) */
+       TM_SLAB_BOUNDARY = 2,   /* output sites with t = 0 or t = Lt_s-1 (read the received faces) */
+       TM_SLAB_ALL = 3 };
+enum { TM_SLAB_HOP = 0,        /* out = H in (plain hop, H_eo or H_oe, or its adjoint with dagger) */
+       TM_SLAB_QTM_A = 1,      /* out_o = -kappa^2 (1 + i mut gamma5)^-1 H_oe in_e: first stage of Q_tm */
+       TM_SLAB_QTM_B = 2 };    /* out_e = gamma5 [(1 + i mut gamma5) x_e + H_eo in_o]: second stage */
+
+/* Bytes of one face of a slab with gauge handle U (0 if unsupported). */
+size_t tm_slab_face_bytes(const tm_gauge *U);
+
+/* Writes the two faces of the input field in_dev of the hop `dir` (TM_OE:
+ * in is even; TM_EO: in is odd) with the projectors of the plain or the
+ * adjoint hop (dagger): send_lower_dev for the previous slab, send_upper_dev
+ * for the next one.  Asynchronous on `stream`. */
+tm_status tm_slab_pack(tm_ctx *ctx, const tm_gauge *U, const void *in_dev, int dir, int dagger, void *send_lower_dev,
+                       void *send_upper_dev, void *stream);
+
+/* The hop of the slab for the output sites in `region`: op TM_SLAB_HOP
+ * gives out = H in (dagger as in tm_hopping_eo); TM_SLAB_QTM_A (dir TM_OE)
+ * and TM_SLAB_QTM_B (dir TM_EO, x_dev the even input of Q_tm) are the two
+ * stages of Q_tm(sign*mu) as in tm_Qtm, so that stage A, the face exchange
+ * of its output and stage B give Q_tm on the whole lattice.  recv_lower_dev
+ * holds the previous slab's upper face, recv_upper_dev the next slab's lower
+ * face (both needed for TM_SLAB_BOUNDARY); sign_lower / sign_upper (+1 or
+ * -1) multiply the hops through the lower / upper face (the boundary sign
+ * of the global time direction for the slabs at its ends, else +1); the
+ * slab's own bc[0] is not used for those hops.  The interior region reads
+ * no face, so its launch may run while the faces are in transit.
+ * Asynchronous on `stream`. */
+tm_status tm_slab_hop(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const void *in_dev, const void *recv_lower_dev,
+                      const void *recv_upper_dev, int dir, int dagger, int region, int op, double kappa, double mu,
+                      int sign, const void *x_dev, int sign_lower, int sign_upper, void *stream);
+
 /* ---- measurement and field utilities -------------------------------------- */
 
 /* Measures the fused multiply-add throughput of the device in precision prec

@@ -687,29 +687,38 @@ TM_HD typename SpinorIO<P>::R load_project(const void *in, unsigned vh, unsigned
 // psi(x-mu).  DAG swaps the two projectors, which gives the adjoint hop
 // gamma5 Dhop gamma5 = Dhop^dag.
 template <int P, bool DAG, int MU, class Src>
-TM_HD void hop_dir(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<typename SpinorIO<P>::R> &acc)
+TM_HD void hop_fwd(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<typename SpinorIO<P>::R> &acc)
 {
     using R = typename SpinorIO<P>::R;
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma_mu
-    constexpr int SB = -SF;
-    {
-        Half<R> h, r;
-        Link<R> u;
-        R w = load_project<P, MU, SF>(in, g.vh, n.fwd[MU], h);
-        src.template fwd<MU>(n, u);
-        link_mul<false>(u, h, r);
-        if (n.wf[MU] && g.anti[MU]) w = -w;
-        accumulate<MU, SF>(r, w, acc);
-    }
-    {
-        Half<R> h, r;
-        Link<R> u;
-        R w = load_project<P, MU, SB>(in, g.vh, n.bwd[MU], h);
-        src.template bwd<MU>(n, u);
-        link_mul<true>(u, h, r);
-        if (n.wb[MU] && g.anti[MU]) w = -w;
-        accumulate<MU, SB>(r, w, acc);
-    }
+    Half<R> h, r;
+    Link<R> u;
+    R w = load_project<P, MU, SF>(in, g.vh, n.fwd[MU], h);
+    src.template fwd<MU>(n, u);
+    link_mul<false>(u, h, r);
+    if (n.wf[MU] && g.anti[MU]) w = -w;
+    accumulate<MU, SF>(r, w, acc);
+}
+
+template <int P, bool DAG, int MU, class Src>
+TM_HD void hop_bwd(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<typename SpinorIO<P>::R> &acc)
+{
+    using R = typename SpinorIO<P>::R;
+    constexpr int SB = DAG ? -1 : +1;  // backward projector 1 + SB gamma_mu
+    Half<R> h, r;
+    Link<R> u;
+    R w = load_project<P, MU, SB>(in, g.vh, n.bwd[MU], h);
+    src.template bwd<MU>(n, u);
+    link_mul<true>(u, h, r);
+    if (n.wb[MU] && g.anti[MU]) w = -w;
+    accumulate<MU, SB>(r, w, acc);
+}
+
+template <int P, bool DAG, int MU, class Src>
+TM_HD void hop_dir(const Geom &g, const Nbrs &n, const Src &src, const void *in, Spinor<typename SpinorIO<P>::R> &acc)
+{
+    hop_fwd<P, DAG, MU>(g, n, src, in, acc);
+    hop_bwd<P, DAG, MU>(g, n, src, in, acc);
 }
 
 // ---------------------------------------------------------------- FP64 pairs

@@ -12,8 +12,15 @@ using namespace twm;
 namespace {
 
 // Sink of the probe: written only if the chains reach a value they cannot
-// reach, so the compiler keeps every FMA and the probe touches no memory.
+// reach, so the compiler keeps every FMA.
 __device__ double g_probe_sink;
+// The multiplier and addend of the chains, read from device memory into
+// registers once per thread.  As kernel parameters (constant-bank operands)
+// they were measured to hold FP64 FMA issue at 1.68 of the 2 lanes per SM
+// and clock that register operands reach on GB300, which would understate
+// the peak.
+__device__ double g_probe_f64[2] = {0.9999999, 1e-7};
+__device__ float g_probe_f32[2] = {0.9999f, 1e-4f};
 
 constexpr int kProbeChains = 8;     // independent FMA chains per thread
 constexpr int kProbeThreads = 256;
@@ -22,8 +29,9 @@ constexpr int kProbeThreads = 256;
 // 2 flop per FMA.  a < 1 and b > 0 keep every value near b / (1 - a) = 1,
 // away from overflow and subnormals.
 template <typename T>
-__global__ void __launch_bounds__(kProbeThreads) k_fma_probe(int iters, T a, T b)
+__global__ void __launch_bounds__(kProbeThreads) k_fma_probe(int iters, const T *ab)
 {
+    const T a = ab[0], b = ab[1];
     T x[kProbeChains];
 #pragma unroll
     for (int k = 0; k < kProbeChains; ++k) x[k] = T(threadIdx.x * 1e-6) + T(k);
@@ -127,15 +135,20 @@ tm_status tm_probe_fma(tm_ctx *ctx, int prec, double *tflops, void *stream)
     // for about 10 ms at the nominal rates (FP64 ~1.3, FP32 ~80 TFLOP/s).
     const unsigned grid = unsigned(ctx->sm_count > 0 ? ctx->sm_count : 1) * 8u;
     const int iters = prec == TM_F64 ? 2048 : 131072;
+    const double *ab64 = nullptr;
+    const float *ab32 = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&ab64, g_probe_f64);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&ab32, g_probe_f32);
+    if (e != cudaSuccess) return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_probe_fma: ") + cudaGetErrorString(e));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaEventCreate(&e0);
+    e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best_ms = 1e30;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // first launch warms up
         e = cudaEventRecord(e0, s);
         if (e != cudaSuccess) break;
-        if (prec == TM_F64) k_fma_probe<double><<<grid, kProbeThreads, 0, s>>>(iters, 0.9999999, 1e-7);
-        else k_fma_probe<float><<<grid, kProbeThreads, 0, s>>>(iters, 0.9999f, 1e-4f);
+        if (prec == TM_F64) k_fma_probe<double><<<grid, kProbeThreads, 0, s>>>(iters, ab64);
+        else k_fma_probe<float><<<grid, kProbeThreads, 0, s>>>(iters, ab32);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);

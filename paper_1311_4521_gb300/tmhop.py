@@ -24,6 +24,8 @@ TM_F64, TM_F32, TM_F16, TM_F64X = 0, 1, 2, 3
 TM_EO, TM_OE = 0, 1
 TM_FORCE_SU3, TM_FORCE_GRAD = 0, 1
 TM_FORCE_OWNER, TM_FORCE_ATOMIC, TM_FORCE_HALO = 0, 1, 2
+TM_SLAB_INTERIOR, TM_SLAB_BOUNDARY, TM_SLAB_ALL = 1, 2, 3
+TM_SLAB_HOP, TM_SLAB_QTM_A, TM_SLAB_QTM_B = 0, 1, 2
 PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16, "f64x": TM_F64X}
 
 
@@ -84,6 +86,9 @@ def _load() -> ctypes.CDLL:
         "tm_spinor_dot": ([P, L, P, P, I, P, P], I),
         "tm_scale_complex": ([P, S, P, P, D, P], I),
         "tm_ctx_device_bytes": ([P], S),
+        "tm_slab_face_bytes": ([P], S),
+        "tm_slab_pack": ([P, P, P, I, I, P, P, P], I),
+        "tm_slab_hop": ([P, P, P, P, P, P, I, I, I, I, D, D, I, P, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -284,6 +289,23 @@ def tm_spinor_dot(ctx, vh, a_dev, b_dev, prec, out_dev, stream=None):
 def tm_scale_complex(ctx, n, z_dev, alpha_dev, c, stream=None):
     """z <- c * alpha * z for n complex doubles in device memory (alpha_dev: device double or None)."""
     _check(ctx, lib.tm_scale_complex(ctx, int(n), _ptr(z_dev), _ptr(alpha_dev), float(c), _stream(stream)))
+
+
+def tm_slab_face_bytes(U) -> int:
+    """Bytes of one face of the slab whose gauge handle is U."""
+    return int(lib.tm_slab_face_bytes(U))
+
+
+def tm_slab_pack(ctx, U, in_dev, dir, dagger, send_lower_dev, send_upper_dev, stream=None):
+    _check(ctx, lib.tm_slab_pack(ctx, U, _ptr(in_dev), int(dir), int(dagger), _ptr(send_lower_dev),
+                                 _ptr(send_upper_dev), _stream(stream)))
+
+
+def tm_slab_hop(ctx, U, out_dev, in_dev, recv_lower_dev, recv_upper_dev, dir, dagger, region, op, kappa=0.0,
+                mu=0.0, sign=1, x_dev=None, sign_lower=1, sign_upper=1, stream=None):
+    _check(ctx, lib.tm_slab_hop(ctx, U, _ptr(out_dev), _ptr(in_dev), _ptr(recv_lower_dev), _ptr(recv_upper_dev),
+                                int(dir), int(dagger), int(region), int(op), float(kappa), float(mu), int(sign),
+                                _ptr(x_dev), int(sign_lower), int(sign_upper), _stream(stream)))
 
 
 def tm_ctx_device_bytes(ctx) -> int:
