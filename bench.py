@@ -132,6 +132,25 @@ def job_throughput(world: int, units_per_rank: int, bytes_per_unit: float, max_m
     return world * units_per_rank * bytes_per_unit / (max_ms * 1e-3) / 1e9
 
 
+def tune_gauge(tmhop, ctx, g) -> dict:
+    """Runs the library's site-map autotuner for a gauge handle and returns
+    its choice: the map, its time per launch, the default map's time and
+    the gain (from the context's tune report)."""
+    tmhop.tm_gauge_tune(ctx.handle, g.handle)
+    out = {"map": tmhop.tm_gauge_map(g.handle)}
+    tag = f"|{g.dims[0]}x{g.dims[1]}x{g.dims[2]}x{g.dims[3]}|prec{g.prec}|recon{g.reconstruct}|"
+    for line in tmhop.tm_ctx_tune_report(ctx.handle).splitlines():
+        if not line.startswith("hop/") or tag not in line.split()[0]:
+            continue
+        for tok in line.split()[1:]:
+            k, _, v = tok.partition("=")
+            if k in ("ms", "linear128_ms", "gain"):
+                out[k] = float(v)
+            elif k == "candidates":
+                out[k] = int(v)
+    return out
+
+
 def load_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -279,8 +298,10 @@ def gpu_arm(args) -> None:
              "how": "tm_probe_fma: 8 CTAs x 256 threads per SM, 8 independent FMA chains per thread, "
                     "best of 3 timed launches of ~10 ms, 2 flop per FMA"}
 
-    # ---- headline: FP64 storage, 18-real links (by default)
+    # ---- headline: FP64 storage, 18-real links (by default); the hop's
+    # site-to-thread map is chosen by the library's autotuner first
     g = ctx.gauge(DIMS, U, prec, recon)
+    site_map = tune_gauge(tmhop, ctx, g)
     src = ctx.pack(psi, prec)
     dst = ctx.empty(vh, prec)
     clocks = ClockSampler(uuid).start()
@@ -313,13 +334,14 @@ def gpu_arm(args) -> None:
         roofline = {"bound": "hbm", "achieved": round(kb_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(kb_gbs / hbm_peak, 4), "traffic": traffic, "kernel": kname,
                     "peak_source": f"{hbm_src} HBM copy bandwidth"}
-    roofline.update({"kernel_a_ms": round(ka_ms, 4), "kernel_b_ms": round(kb_ms, 4),
+    roofline.update({"site_map": site_map, "kernel_a_ms": round(ka_ms, 4), "kernel_b_ms": round(kb_ms, 4),
                      "bytes_per_launch": vh * ab["kernel_b"], "flops_per_launch": vh * (HOP_FLOPS + 96)})
 
     # ---- FP64-accurate operator in double-float storage and arithmetic (not the headline)
     f64x = None
     if prec == "f64" and not args.no_table:
         gx = ctx.gauge(DIMS, U, "f64x", 18)
+        tune_gauge(tmhop, ctx, gx)
         sx, dx = ctx.pack(psi, "f64x"), ctx.empty(vh, "f64x")
         n = max(1, min(args.steps, args.table_steps))
         tx, ax_ms, bx_ms = time_qtm(ctx, tmhop, torch, gx, sx, dx, n, args.warmup, barrier)
@@ -369,6 +391,7 @@ def gpu_arm(args) -> None:
     if not args.no_table:
         for tp, tr in (("f64", 12), ("f64x", 18), ("f64x", 12), ("f32", 18), ("f32", 12), ("f16", 12)):
             gp = ctx.gauge(DIMS, U, tp, tr)
+            gmap = tune_gauge(tmhop, ctx, gp)
             sp = ctx.pack(psi, tp)
             dp = ctx.empty(vh, tp)
             n = max(1, min(args.steps, args.table_steps))
@@ -381,7 +404,8 @@ def gpu_arm(args) -> None:
                 "gflops": round(vh * QTM_FLOPS / (step_ms * 1e-3) / 1e9, 1),
                 "kernel_b_ms": round(b_ms, 4), "kernel_b_GBps": round(bgbs, 1),
                 "kernel_b_hbm_frac": round(bgbs / hbm_peak, 4),
-                "kernel_b_nominal_frac": round(bgbs / HBM_NOMINAL_GBS, 4), "kernel_a_ms": round(a_ms, 4)}
+                "kernel_b_nominal_frac": round(bgbs / HBM_NOMINAL_GBS, 4), "kernel_a_ms": round(a_ms, 4),
+                "site_map": gmap}
             gp.close()
             del sp, dp
 

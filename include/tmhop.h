@@ -94,10 +94,20 @@ tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on);
 
 /* Text report of the launch configurations the context has chosen so far,
  * one line per batch shape: "<key> nrb=<pass width> cap=<CTA cap> ms3=<time
- * of three launches at selection>".  Writes at most size bytes including the
+ * of three launches at selection>", and one per lattice tuned by
+ * tm_gauge_tune: "hop/<cache key> map=<map> ms=<per launch> linear128_ms=<the
+ * default map's> gain=<ratio> candidates=<n>" (or "map=<map> (cache)").  Writes at most size bytes including the
  * terminating NUL (truncating) and returns the size the full report needs;
  * buf may be NULL to ask for that size. */
 size_t tm_ctx_tune_report(const tm_ctx *ctx, char *buf, size_t size);
+
+/* File in which tm_gauge_tune keeps its choices, one line "<key> <map>
+ * <ms>" per lattice, keyed by "<GPU name>|<Lx>x<Ly>x<Lz>x<Lt>|prec<p>|recon<r>
+ * |nrhs1" (NULL or "": no file).  A context starts with the path in the
+ * environment variable TMHOP_TUNE_CACHE, if set.  With a cache file and
+ * autotuning on, tm_gauge_create gives a new handle the cached map of its
+ * lattice. */
+tm_status tm_ctx_set_tune_cache(tm_ctx *ctx, const char *path);
 
 /* ---- fields --------------------------------------------------------------- */
 
@@ -132,6 +142,31 @@ tm_status tm_gauge_create(tm_ctx *ctx, const int dims[4], const double *U_dev, i
 void tm_gauge_destroy(tm_gauge *g);
 /* Bytes of device memory held by the handle's link storage. */
 size_t tm_gauge_bytes(const tm_gauge *g);
+
+/* Site-to-thread maps of the hop launches (tm_hopping_eo, tm_Qtm, tm_force,
+ * tm_solve_eo) on the handle's lattice.  "linear<B>" gives CTAs of B threads
+ * consecutive even-odd sites (whole rows along x, then y, z, t); "box<a>x<b>
+ * x<c>x<d>" gives each CTA a box of a x b x c x d sites along (x half-row,
+ * y, z, t), a..d powers of two dividing (Lx/2, Ly, Lz, Lt), 32 to 128 sites.
+ * The analogue of the paper's hopping-order index and thread-distribution
+ * studies (Secs. 2.2, 2.3): every map computes every site with the same
+ * arithmetic, so outputs are bit-identical whatever the map; only the
+ * memory access order, and with it the time, changes.  Default: linear128.
+ *
+ * tm_gauge_tune chooses the map: with a cache entry for the lattice (see
+ * tm_ctx_set_tune_cache) it takes that; otherwise, with autotuning on, it
+ * times the linear maps of 128 and 64 threads and every box of 64 or 128
+ * sites with at least 4 sites along the half-row and at most 8 along y, z, t
+ * (each: median of three rounds of two launches of the even-output hop with
+ * the fused Q_tm update), keeps the fastest and appends it to the cache file;
+ * with autotuning off it sets linear128.  It uses the context's workspace
+ * and synchronises `stream`, so call it outside stream capture.
+ * tm_gauge_set_map sets a map by name (TM_ERR_ARG if it does not fit the
+ * lattice); tm_gauge_map writes the current map's name (like
+ * tm_ctx_tune_report: at most size bytes, returns the size needed). */
+tm_status tm_gauge_tune(tm_ctx *ctx, tm_gauge *U, void *stream);
+tm_status tm_gauge_set_map(tm_ctx *ctx, tm_gauge *U, const char *name);
+size_t tm_gauge_map(const tm_gauge *U, char *buf, size_t size);
 
 /* ---- operator ------------------------------------------------------------ */
 

@@ -1,6 +1,7 @@
 // tm_api.cu -- the C ABI of include/tmhop.h: contexts, gauge handles,
 // packed fields, the hopping matrix and Q_tm.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "tm_internal.h"
@@ -93,6 +94,7 @@ tm_status tm_ctx_create(tm_ctx **out, int device)
     tm_ctx *ctx = new tm_ctx;
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (const char *cache = getenv("TMHOP_TUNE_CACHE")) ctx->tune_cache = cache;
     *out = ctx;
     return TM_OK;
 }
@@ -130,6 +132,7 @@ size_t tm_ctx_tune_report(const tm_ctx *ctx, char *buf, size_t size)
                  kv.second.second, ms == ctx->tuned_ms.end() ? 0.0 : double(ms->second));
         rep += line;
     }
+    for (const auto &kv : ctx->tuned_maps) rep += "hop/" + kv.first + " " + kv.second + "\n";
     if (buf && size > 0) {
         const size_t n = rep.size() < size - 1 ? rep.size() : size - 1;
         memcpy(buf, rep.data(), n);
@@ -214,6 +217,7 @@ tm_status tm_gauge_create(tm_ctx *ctx, const int dims[4], const double *U_dev, i
         delete h;
         return cuda_fail(ctx, e, "tm_gauge_create: pack");
     }
+    tm_apply_cached_map(ctx, h);
     *out = h;
     return TM_OK;
 }
@@ -235,7 +239,7 @@ tm_status tm_hopping_eo(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const voi
     if (dir != TM_EO && dir != TM_OE) return fail(ctx, TM_ERR_ARG, "tm_hopping_eo: dir must be TM_EO or TM_OE");
     if (out_dev == in_dev) return fail(ctx, TM_ERR_ARG, "tm_hopping_eo: out and in must not overlap");
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, dagger != 0, dir, U->links, in_dev, out_dev, nullptr,
-                            coef_plain(), (cudaStream_t)stream, 128));
+                            coef_plain(), (cudaStream_t)stream, U->map));
     return TM_OK;
 }
 
@@ -253,10 +257,10 @@ tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in
     cudaStream_t s = (cudaStream_t)stream;
     tm_trace_mark(ctx, 0, s);
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, in_e_dev, tmp, nullptr,
-                            coef_qtm_a_scaled(kappa, mut), s, 128));
+                            coef_qtm_a_scaled(kappa, mut), s, U->map));
     tm_trace_mark(ctx, 1, s);
     TM_CUDA(ctx, launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, tmp, out_e_dev, in_e_dev,
-                            coef_qtm_b_unit(mut), s, 128));
+                            coef_qtm_b_unit(mut), s, U->map));
     tm_trace_mark(ctx, 2, s);
     return TM_OK;
 }

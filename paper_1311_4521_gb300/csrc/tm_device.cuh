@@ -159,6 +159,97 @@ TM_HD void neighbours(const Geom &g, int p, unsigned i, Nbrs &n)
     n.bwd[0] = n.wb[0] ? i + (g.lt - 1) * g.st : i - g.st;
 }
 
+// ---------------------------------------------------------------- site maps
+// Division by a divisor fixed on the host: q = (umulhi(n, m) + n) >> s with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1, exact for every
+// n < 2^31 (the "round-up" method of Granlund and Montgomery, PLDI 1994).
+struct FastDiv {
+    unsigned d = 1, m = 0, s = 0;
+    FastDiv() = default;
+    explicit FastDiv(unsigned div) : d(div)
+    {
+        while ((1ull << s) < d) ++s;
+        m = unsigned(((1ull << 32) * ((1ull << s) - d)) / d + 1);
+    }
+    TM_HD unsigned div(unsigned n) const
+    {
+#if defined(__CUDA_ARCH__)
+        const unsigned hi = __umulhi(n, m);
+#else
+        const unsigned hi = unsigned((static_cast<unsigned long long>(n) * m) >> 32);
+#endif
+        return (hi + n) >> s;
+    }
+};
+
+// Which output site (even-odd index) thread k of CTA b handles.  Linear:
+// site b * block + k (a CTA covers consecutive sites: with Lx/2 sites per
+// half-row, whole y rows at one z, t).  Tiled: a CTA covers a box of
+// 2^lg[0] x 2^lg[1] x 2^lg[2] x 2^lg[3] sites in (x-half, y, z, t), every
+// extent dividing the lattice's, and the boxes are numbered x-half fastest.
+// A box keeps more of each site's 8 neighbours inside the CTA's own sites
+// than a run of whole rows (e.g. 16x2x2x2 against 16x8x1x1: 62 % against
+// 47 % of the neighbour loads), so more of them may hit in L1.  Every map
+// covers every site exactly once and the per-site arithmetic does not
+// depend on the map, so all maps give bit-identical results.
+struct SiteMap {
+    int tiled = 0;
+    unsigned block = 128;           // threads per CTA
+    unsigned lg[4] = {0, 0, 0, 0};  // log2 of the box extents (tiled)
+    FastDiv nbx, nby, nbz;          // boxes along x-half, y, z (tiled)
+};
+
+TM_HD unsigned map_site(const Geom &g, const SiteMap &m, unsigned b, unsigned k)
+{
+    if (!m.tiled) return b * m.block + k;
+    const unsigned kx = k & ((1u << m.lg[0]) - 1);
+    const unsigned ky = (k >> m.lg[0]) & ((1u << m.lg[1]) - 1);
+    const unsigned kz = (k >> (m.lg[0] + m.lg[1])) & ((1u << m.lg[2]) - 1);
+    const unsigned kt = k >> (m.lg[0] + m.lg[1] + m.lg[2]);
+    const unsigned r1 = m.nbx.div(b), bx = b - r1 * m.nbx.d;
+    const unsigned r2 = m.nby.div(r1), by = r1 - r2 * m.nby.d;
+    const unsigned bt = m.nbz.div(r2), bz = r2 - bt * m.nbz.d;
+    const unsigned x = (bx << m.lg[0]) + kx, y = (by << m.lg[1]) + ky;
+    const unsigned z = (bz << m.lg[2]) + kz, t = (bt << m.lg[3]) + kt;
+    return x + unsigned(g.hx) * (y + unsigned(g.ly) * (z + unsigned(g.lz) * t));
+}
+
+// CTAs a map needs; the linear map of `block` threads; a tiled map with box
+// extents 2^lg[d] (false if they do not divide the lattice or the box has
+// fewer than 32 or more than 128 sites, the most the hop kernels are
+// compiled for).
+inline unsigned map_grid(const Geom &g, const SiteMap &m)
+{
+    if (!m.tiled) return (g.vh + m.block - 1) / m.block;
+    return m.nbx.d * m.nby.d * m.nbz.d * (unsigned(g.lt) >> m.lg[3]);
+}
+
+inline SiteMap linear_map(unsigned block)
+{
+    SiteMap m;
+    m.block = block;
+    return m;
+}
+
+inline bool tiled_map(const Geom &g, const unsigned lg[4], SiteMap &m)
+{
+    const unsigned ext[4] = {unsigned(g.hx), unsigned(g.ly), unsigned(g.lz), unsigned(g.lt)};
+    unsigned threads = 1;
+    for (int d = 0; d < 4; ++d) {
+        if (lg[d] > 10 || ext[d] % (1u << lg[d])) return false;
+        threads <<= lg[d];
+    }
+    if (threads < 32 || threads > 128) return false;
+    m = SiteMap();
+    m.tiled = 1;
+    m.block = threads;
+    for (int d = 0; d < 4; ++d) m.lg[d] = lg[d];
+    m.nbx = FastDiv(ext[0] >> lg[0]);
+    m.nby = FastDiv(ext[1] >> lg[1]);
+    m.nbz = FastDiv(ext[2] >> lg[2]);
+    return true;
+}
+
 // ---------------------------------------------------------------- loads
 #if defined(__CUDA_ARCH__)
 template <typename T> __device__ __forceinline__ T ld_keep(const T *p) { return __ldg(p); }

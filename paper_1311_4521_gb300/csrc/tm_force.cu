@@ -179,11 +179,11 @@ extern "C" tm_status tm_force_ex(tm_ctx *ctx, const tm_gauge *U, double *F_dev, 
     cudaStream_t s = (cudaStream_t)stream;
     // Z = M_oo^-1 H_oe X, Y = Q X, B = gamma5 (M_oo^-1)^dag H_oe Y
     cudaError_t e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, X_e_dev, Zo, nullptr,
-                               coef_qtm_a(mut), s, 128);
+                               coef_qtm_a(mut), s, U->map);
     if (e == cudaSuccess)
-        e = launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, Zo, Ye, X_e_dev, coef_qtm_b(kappa, mut), s, 128);
+        e = launch_hop(U->geom, U->prec, U->recon, false, TM_EO, U->links, Zo, Ye, X_e_dev, coef_qtm_b(kappa, mut), s, U->map);
     if (e == cudaSuccess)
-        e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, Ye, Bo, nullptr, coef_force_b(mut), s, 128);
+        e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, Ye, Bo, nullptr, coef_force_b(mut), s, U->map);
     const double k2 = kappa * kappa;
     if (e == cudaSuccess && scheme == TM_FORCE_OWNER) {
         switch (U->prec * 100 + U->recon) {

@@ -26,6 +26,8 @@ struct tm_ctx {
     int autotune = 1;                // time launch configurations on first use
     std::map<std::string, std::pair<int, unsigned>> tuned;  // batched hop: key -> (pass width, CTA cap)
     std::map<std::string, float> tuned_ms;                  // and the winner's time for 3 launches
+    std::map<std::string, std::string> tuned_maps;          // single-lattice hop: key -> chosen map (tm_gauge_tune)
+    std::string tune_cache;          // autotune cache file ("" = none; TMHOP_TUNE_CACHE at creation)
     void *stage = nullptr;           // device staging slots of tm_Qtm_host (grow-only)
     size_t stage_bytes = 0;
     cudaStream_t copy_in = nullptr;  // copy streams of tm_Qtm_host (created on first use)
@@ -95,7 +97,12 @@ struct tm_gauge {
     twm::Geom geom{};
     void *links = nullptr;
     size_t bytes = 0;
+    twm::SiteMap map{};   // site-to-thread map of this lattice's hop launches (tm_gauge_tune)
+    std::string map_name = "linear128";
 };
+
+// Gives U the site map its lattice has in the context's tune cache, if any.
+void tm_apply_cached_map(tm_ctx *ctx, tm_gauge *U);
 
 namespace twm {
 
@@ -103,6 +110,10 @@ namespace twm {
 bool make_geom(const int dims[4], const int bc[4], Geom &g);
 
 // Launchers (tm_kernels.cu).  All enqueue on `s` and return the launch status.
+// The hop with the given site-to-thread map, or with the linear map of
+// `block` threads per CTA.
+cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_parity, const void *links,
+                       const void *in, void *out, const void *x, const Coef &k, cudaStream_t s, const SiteMap &m);
 cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_parity, const void *links,
                        const void *in, void *out, const void *x, const Coef &k, cudaStream_t s, int block);
 cudaError_t launch_pack_gauge(const Geom &g, int prec, int recon, const double *U, void *links, cudaStream_t s);

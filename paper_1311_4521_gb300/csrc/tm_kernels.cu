@@ -60,10 +60,10 @@ Coef coef_qtm_b_unit(double mut)
 template <int P, int RECON, bool DAG, bool HASX>
 __global__ void __launch_bounds__(128, TM_HOP_MINB(P)) k_hop(Geom g, int p, const typename LinkIO<P, RECON>::V *__restrict__ links,
                                              const void *__restrict__ in, void *__restrict__ out,
-                                             const void *__restrict__ x, Coef k)
+                                             const void *__restrict__ x, Coef k, SiteMap m)
 {
     using R = typename SpinorIO<P>::R;
-    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned i = map_site(g, m, blockIdx.x, threadIdx.x);
     if (i >= g.vh) return;
     Spinor<R> acc, o;
     hop_site<P, RECON, DAG>(g, p, i, links, in, acc);
@@ -79,29 +79,35 @@ __global__ void __launch_bounds__(128, TM_HOP_MINB(P)) k_hop(Geom g, int p, cons
 
 template <int P, int RECON>
 static cudaError_t hop_dispatch(const Geom &g, bool dag, int p, const void *links, const void *in, void *out,
-                                const void *x, const Coef &k, cudaStream_t s, int block)
+                                const void *x, const Coef &k, cudaStream_t s, const SiteMap &m)
 {
     using V = typename LinkIO<P, RECON>::V;
     const V *l = static_cast<const V *>(links);
-    unsigned grid = (g.vh + block - 1) / block;
+    const unsigned grid = map_grid(g, m);
     auto kern = dag ? (x ? k_hop<P, RECON, true, true> : k_hop<P, RECON, true, false>)
                     : (x ? k_hop<P, RECON, false, true> : k_hop<P, RECON, false, false>);
-    kern<<<grid, block, 0, s>>>(g, p, l, in, out, x, k);
+    kern<<<grid, m.block, 0, s>>>(g, p, l, in, out, x, k, m);
     return cudaGetLastError();
+}
+
+cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_parity, const void *links,
+                       const void *in, void *out, const void *x, const Coef &k, cudaStream_t s, const SiteMap &m)
+{
+    if (g.vh == 0) return cudaSuccess;
+    if (prec == F64 && recon == 18) return hop_dispatch<F64, 18>(g, dag, out_parity, links, in, out, x, k, s, m);
+    if (prec == F64 && recon == 12) return hop_dispatch<F64, 12>(g, dag, out_parity, links, in, out, x, k, s, m);
+    if (prec == F32 && recon == 18) return hop_dispatch<F32, 18>(g, dag, out_parity, links, in, out, x, k, s, m);
+    if (prec == F32 && recon == 12) return hop_dispatch<F32, 12>(g, dag, out_parity, links, in, out, x, k, s, m);
+    if (prec == F16 && recon == 12) return hop_dispatch<F16, 12>(g, dag, out_parity, links, in, out, x, k, s, m);
+    if (prec == F64X && recon == 18) return hop_dispatch<F64X, 18>(g, dag, out_parity, links, in, out, x, k, s, m);
+    if (prec == F64X && recon == 12) return hop_dispatch<F64X, 12>(g, dag, out_parity, links, in, out, x, k, s, m);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_parity, const void *links,
                        const void *in, void *out, const void *x, const Coef &k, cudaStream_t s, int block)
 {
-    if (g.vh == 0) return cudaSuccess;
-    if (prec == F64 && recon == 18) return hop_dispatch<F64, 18>(g, dag, out_parity, links, in, out, x, k, s, block);
-    if (prec == F64 && recon == 12) return hop_dispatch<F64, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
-    if (prec == F32 && recon == 18) return hop_dispatch<F32, 18>(g, dag, out_parity, links, in, out, x, k, s, block);
-    if (prec == F32 && recon == 12) return hop_dispatch<F32, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
-    if (prec == F16 && recon == 12) return hop_dispatch<F16, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
-    if (prec == F64X && recon == 18) return hop_dispatch<F64X, 18>(g, dag, out_parity, links, in, out, x, k, s, block);
-    if (prec == F64X && recon == 12) return hop_dispatch<F64X, 12>(g, dag, out_parity, links, in, out, x, k, s, block);
-    return cudaErrorInvalidValue;
+    return launch_hop(g, prec, recon, dag, out_parity, links, in, out, x, k, s, linear_map(unsigned(block)));
 }
 
 // ------------------------------------------------------------------ layouts

@@ -64,12 +64,12 @@ extern "C" tm_status tm_solve_eo(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     // c_e = gamma5 (b_e + kappa H_eo t_o)
     if (e == cudaSuccess)
         e = launch_hop(g, F64, U_hi->recon, false, TM_EO, U_hi->links, t_o, c_e, b_e,
-                       Coef{kappa, 0, -kappa, 0, 1, 0, -1, 0}, s, 128);
+                       Coef{kappa, 0, -kappa, 0, 1, 0, -1, 0}, s, U_hi->map);
     // src = Q(-mu) c_e = Q^dag gamma5 bhat_e
     if (e == cudaSuccess)
-        e = launch_hop(g, F64, U_hi->recon, false, TM_OE, U_hi->links, c_e, t_o, nullptr, coef_qtm_a_scaled(kappa, -mut), s, 128);
+        e = launch_hop(g, F64, U_hi->recon, false, TM_OE, U_hi->links, c_e, t_o, nullptr, coef_qtm_a_scaled(kappa, -mut), s, U_hi->map);
     if (e == cudaSuccess)
-        e = launch_hop(g, F64, U_hi->recon, false, TM_EO, U_hi->links, t_o, src, c_e, coef_qtm_b_unit(-mut), s, 128);
+        e = launch_hop(g, F64, U_hi->recon, false, TM_EO, U_hi->links, t_o, src, c_e, coef_qtm_b_unit(-mut), s, U_hi->map);
     if (e != cudaSuccess) {
         ctx->err = std::string("tm_solve_eo: source: ") + cudaGetErrorString(e);
         return TM_ERR_CUDA;
@@ -78,7 +78,7 @@ extern "C" tm_status tm_solve_eo(tm_ctx *ctx, const tm_gauge *U_hi, const tm_gau
     if (cg != TM_OK && cg != TM_ERR_NOT_CONVERGED) return cg;
     // x_o = M_oo^-1 (b_o + kappa H_oe x_e)
     e = launch_hop(g, F64, U_hi->recon, false, TM_OE, U_hi->links, x_e, x_o, b_o,
-                   Coef{kappa * d, -kappa * mut * d, kappa * d, kappa * mut * d, d, -mut * d, d, mut * d}, s, 128);
+                   Coef{kappa * d, -kappa * mut * d, kappa * d, kappa * mut * d, d, -mut * d, d, mut * d}, s, U_hi->map);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         ctx->err = std::string("tm_solve_eo: reconstruction: ") + cudaGetErrorString(e);

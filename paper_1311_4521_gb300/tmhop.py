@@ -87,6 +87,10 @@ def _load() -> ctypes.CDLL:
         "tm_scale_complex": ([P, S, P, P, D, P], I),
         "tm_ctx_device_bytes": ([P], S),
         "tm_slab_face_bytes": ([P], S),
+        "tm_ctx_set_tune_cache": ([P, ctypes.c_char_p], I),
+        "tm_gauge_tune": ([P, P, P], I),
+        "tm_gauge_set_map": ([P, P, ctypes.c_char_p], I),
+        "tm_gauge_map": ([P, ctypes.c_char_p, S], S),
         "tm_slab_pack": ([P, P, P, I, I, P, P, P], I),
         "tm_slab_hop": ([P, P, P, P, P, P, I, I, I, I, D, D, I, P, I, I, P], I),
     }
@@ -289,6 +293,28 @@ def tm_spinor_dot(ctx, vh, a_dev, b_dev, prec, out_dev, stream=None):
 def tm_scale_complex(ctx, n, z_dev, alpha_dev, c, stream=None):
     """z <- c * alpha * z for n complex doubles in device memory (alpha_dev: device double or None)."""
     _check(ctx, lib.tm_scale_complex(ctx, int(n), _ptr(z_dev), _ptr(alpha_dev), float(c), _stream(stream)))
+
+
+def tm_ctx_set_tune_cache(ctx, path) -> None:
+    """Autotune cache file of the context (None: no file)."""
+    _check(ctx, lib.tm_ctx_set_tune_cache(ctx, None if path is None else str(path).encode()))
+
+
+def tm_gauge_tune(ctx, U, stream=None) -> None:
+    """Chooses the hop's site-to-thread map for the handle's lattice (cache, else timing)."""
+    _check(ctx, lib.tm_gauge_tune(ctx, U, _stream(stream)))
+
+
+def tm_gauge_set_map(ctx, U, name: str) -> None:
+    _check(ctx, lib.tm_gauge_set_map(ctx, U, name.encode()))
+
+
+def tm_gauge_map(U) -> str:
+    """Name of the handle's current site-to-thread map."""
+    n = lib.tm_gauge_map(U, None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib.tm_gauge_map(U, buf, n)
+    return buf.value.decode()
 
 
 def tm_slab_face_bytes(U) -> int:
