@@ -92,6 +92,22 @@ tm_status tm_ctx_trace(tm_ctx *ctx, void *const *events, int nevents);
  * context's lifetime; off, a fixed configuration is used. */
 tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on);
 
+/* Fixes the configuration of the batched hop (tm_Qtm_batch,
+ * tm_cg_QdagQ_batch) instead of letting the autotuner choose it.  code % 10
+ * is the pass width: 1 links streamed from memory, work items (tile, rhs);
+ * 0 the same with the right-hand sides of a tile on consecutive CTAs, so
+ * that they share the links through L2; 2 or 4 the tile's links staged in
+ * shared memory once and applied to 2 or 4 right-hand sides at a time.
+ * code / 10 + 1 is the number of right-hand sides each thread computes (2:
+ * one link load for both and twice the neighbour loads in flight; FP32 and
+ * FP16 storage only).  Valid codes: 0, 1, 2, 4, 10, 12, 14; a code that a
+ * storage format does not have (2, 10, 12, 14 for TM_F64 and TM_F64X, e.g.
+ * the FP64 reliable updates of a mixed-precision batched solve) is ignored
+ * for that format, which the autotuner then configures.  cap: at most this
+ * many persistent CTAs (0: one per work item).  code = -1 returns to the
+ * autotuner. */
+tm_status tm_ctx_set_batch_config(tm_ctx *ctx, int code, unsigned cap);
+
 /* Text report of the launch configurations the context has chosen so far,
  * one line per batch shape: "<key> nrb=<pass width> cap=<CTA cap> ms3=<time
  * of three launches at selection>", and one per lattice tuned by

@@ -264,6 +264,11 @@ std::vector<int> nrb_candidates(int prec, int recon, int nrhs_max)
     c.push_back(0);
     if (prec != F64 && prec != F64X) c.push_back(2);
     c.push_back(4);
+    if (prec == F32 || prec == F16) {   // two right-hand sides per thread
+        c.push_back(10);
+        c.push_back(12);
+        c.push_back(14);
+    }
     (void)recon;
     return c;
 }
@@ -273,12 +278,13 @@ cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_
                         cudaStream_t st, std::vector<BGroup> &host)
 {
     host = tmpl;
-    const unsigned ts = nrb > 1 ? BT / nrb : BT;
+    const int w = code_nrb(nrb), rpt = code_rpt(nrb);
+    const unsigned ts = w > 1 ? BT / w : BT;
     unsigned item = 0;
     for (auto &g : host) {
         g.item0 = item;
         g.ntiles = cdiv(g.g.vh, ts);
-        item += nrb <= 1 ? g.ntiles * unsigned(g.nrhs) : g.ntiles;
+        item += w <= 1 ? g.ntiles * cdiv(unsigned(g.nrhs), unsigned(rpt)) : g.ntiles;
     }
     t.nrb = nrb;
     t.nitems = item;
@@ -328,6 +334,15 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     }
     const unsigned sms = unsigned(std::max(1, ctx->sm_count));
     std::vector<BGroup> host;
+    if (ctx->batch_code >= 0) {   // a configuration set by the caller, where this format has it
+        const std::vector<int> ok = nrb_candidates(prec, recon, std::max(nrhs_max, 2));
+        if (std::find(ok.begin(), ok.end(), ctx->batch_code) != ok.end()) {
+            cudaError_t e = build_table(tmpl, ctx->batch_code, ctx->batch_cap ? ctx->batch_cap : 1u << 30, out, dev,
+                                        st, host);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            return e;
+        }
+    }
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
         cudaError_t e = build_table(tmpl, it->second.first, it->second.second, out, dev, st, host);
@@ -398,6 +413,16 @@ tm_status group_systems(tm_ctx *ctx, int nsys, const tm_gauge *const *U, std::ve
 
 }  // namespace
 
+extern "C" tm_status tm_ctx_set_batch_config(tm_ctx *ctx, int code, unsigned cap)
+{
+    if (!ctx) return TM_ERR_ARG;
+    if (code != -1 && code != 0 && code != 1 && code != 2 && code != 4 && code != 10 && code != 12 && code != 14)
+        return tm_fail(ctx, TM_ERR_ARG, "tm_ctx_set_batch_config: code must be -1, 0, 1, 2, 4, 10, 12 or 14");
+    ctx->batch_code = code;
+    ctx->batch_cap = cap;
+    return TM_OK;
+}
+
 extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *U, void *const *out_e,
                                   const void *const *in_e, double kappa, double mu, int sign, void *stream)
 {
@@ -425,7 +450,8 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     // The batch as the device tables describe it: handles (with their links
     // and sizes), fields, precision and stream.  A repeated call with the same
     // batch finds its tables and temporaries in place and only launches.
-    std::vector<uintptr_t> sig{uintptr_t(prec), uintptr_t(recon), uintptr_t(nsys), uintptr_t(s)};
+    std::vector<uintptr_t> sig{uintptr_t(prec), uintptr_t(recon), uintptr_t(nsys), uintptr_t(s),
+                               uintptr_t(ctx->batch_code + 1), uintptr_t(ctx->batch_cap)};
     for (int k = 0; k < nsys; ++k) {
         sig.push_back(uintptr_t(U[k]));
         sig.push_back(uintptr_t(U[k]->links));
@@ -649,7 +675,7 @@ extern "C" tm_status tm_cg_QdagQ_batch(tm_ctx *ctx, int nsys, const tm_gauge *co
         k_batch_finish<<<nsys, BLA, 0, q>>>(SY, nsys, tile_sites, op, gate);
         return cudaGetLastError();
     };
-    auto hop_tile = [&](const HopTable &t) { return unsigned(t.nrb > 1 ? BT / t.nrb : BT); };
+    auto hop_tile = [&](const HopTable &t) { return unsigned(code_nrb(t.nrb) > 1 ? BT / code_nrb(t.nrb) : BT); };
     // ax = Q^dag Q x in FP64 for the systems the gate lets through
     auto qdagq_hi = [&](int gate, cudaStream_t q) {
         cudaError_t r = bhop(F64, B.recon_hi, B.hi, SY, 1, R_X, R_THI, -1, coef_qtm_a_scaled(kappa, mut), BH_PLAIN, gate, q);

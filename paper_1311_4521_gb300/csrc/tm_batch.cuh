@@ -25,6 +25,14 @@ struct BGroup {
 };
 
 constexpr int BT = 128;   // threads per CTA of the batched hop
+// Resident CTAs per SM the batched hop is compiled for, with one and with two
+// right-hand sides per thread (registers per thread <= 65536 / (128 x this)).
+#ifndef TM_BATCH_MINB
+#define TM_BATCH_MINB 4
+#endif
+#ifndef TM_BATCH_MINB_RPT2
+#define TM_BATCH_MINB_RPT2 4
+#endif
 
 // What the batched hop does with its result: store it (PLAIN), store it and
 // reduce |out|^2 per (system, tile) (NORM), or, as the last hop of
@@ -69,7 +77,8 @@ __device__ __forceinline__ int find_group(const BGroup *gr, int ng, const unsign
 
 
 struct HopTable {
-    int nrb = 1;            // right-hand sides per pass (1: no link staging)
+    int nrb = 1;            // configuration code: pass width (code % 10; <= 1: no link staging) and
+                            // right-hand sides per thread (code / 10 + 1)
     unsigned grid = 0;      // persistent CTAs
     unsigned nitems = 0;
     BGroup *dev = nullptr;  // device copy of the groups
@@ -88,11 +97,64 @@ cudaError_t batch_hop_f32_18(const HopTable &t, const BSys *sys, int parity, int
 cudaError_t batch_hop_f16(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k,
                           int mode, int gate, cudaStream_t st);
 
+// Configuration codes of the batched hop: code % 10 is the pass width NRB,
+// code / 10 + 1 the right-hand sides each thread computes (RPT).
+__host__ __device__ constexpr int code_nrb(int code) { return code % 10; }
+__host__ __device__ constexpr int code_rpt(int code) { return code / 10 + 1; }
+
+// The output of one site for one system: the epilogue, then either the store
+// (and |out|^2 for BH_NORM) or the solver update of BH_UPDATE; returns the
+// site's contribution to the system's partial.
+template <int P, int MODE>
+__device__ __forceinline__ double batch_site_out(const BSys *S, unsigned vh, unsigned i,
+                                                 const Spinor<typename SpinorIO<P>::R> &acc, const Coef &k, int rout,
+                                                 int rx)
+{
+    using R = typename SpinorIO<P>::R;
+    Spinor<R> o;
+    if (rx >= 0) {
+        Spinor<R> xs;
+        SpinorIO<P>::load(S->f[rx], vh, i, xs);
+        epilogue(k, acc, &xs, o);
+    } else {
+        epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
+    }
+    if (MODE == BH_UPDATE) {
+        constexpr int PY = P == F16 ? F32 : P;
+        using RY = typename SpinorIO<PY>::R;
+        const double alpha = S->s->alpha;
+        Spinor<R> pv, rv;
+        Spinor<RY> yv;
+        SpinorIO<P>::load(S->f[R_P], vh, i, pv);
+        SpinorIO<P>::load(S->f[R_R], vh, i, rv);
+        SpinorIO<PY>::load(S->f[R_Y], vh, i, yv);
+        const R a = to_R<R>(alpha);
+        const RY ay = to_R<RY>(alpha);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                yv[sp][c].re += ay * RY(pv[sp][c].re);
+                yv[sp][c].im += ay * RY(pv[sp][c].im);
+                rv[sp][c].re -= a * o[sp][c].re;
+                rv[sp][c].im -= a * o[sp][c].im;
+            }
+        SpinorIO<PY>::store(S->f[R_Y], vh, i, yv);
+        SpinorIO<P>::store(S->f[R_R], vh, i, rv);
+        return norm2(rv);
+    }
+    SpinorIO<P>::store(S->f[rout], vh, i, o);
+    return MODE == BH_NORM ? norm2(o) : 0.0;
+}
+
 // NRB: 1 streams links, items (tile, rhs) with the right-hand side fastest;
 // 0 the same with default-cached links (L2 sharing); >= 2 stages the tile's
 // links in shared memory and sweeps the right-hand sides NRB at a time.
-template <int P, int RECON, int NRB, int MODE>
-__global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ groups, int ngroups, unsigned nitems,
+// RPT = 2: each thread computes two right-hand sides of its site with one
+// load of each link (items (tile, pair of rhs) for NRB <= 1; NRB pairs per
+// pass otherwise), which doubles the neighbour loads it has in flight.
+template <int P, int RECON, int NRB, int MODE, int RPT>
+__global__ void __launch_bounds__(BT, RPT == 1 ? TM_BATCH_MINB : TM_BATCH_MINB_RPT2) k_batch_hop(const BGroup *__restrict__ groups, int ngroups, unsigned nitems,
                                                   const BSys *__restrict__ sys, int parity, int rin, int rout, int rx,
                                                   Coef k, int gate)
 {
@@ -102,7 +164,7 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
     constexpr int TS = NRB > 1 ? BT / NRB : BT;
     __shared__ V tile[NRB > 1 ? 8 * L::NCHUNK * TS : 1];
     __shared__ unsigned bwd_idx[NRB > 1 ? 4 * TS : 1];
-    __shared__ double red[BT / 32];
+    __shared__ double red[RPT][BT / 32];
     __shared__ unsigned first[STAGE_MAX];
     const unsigned tx = threadIdx.x % TS, ty = threadIdx.x / TS;
     const unsigned *staged = ngroups <= STAGE_MAX ? first : nullptr;
@@ -114,7 +176,8 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
         const BGroup &G = groups[find_group(groups, ngroups, staged, item)];
         const unsigned rel = item - G.item0;
-        const unsigned tno = NRB <= 1 ? rel / unsigned(G.nrhs) : rel;
+        const unsigned nsets = (unsigned(G.nrhs) + RPT - 1) / RPT;   // items per tile for NRB <= 1
+        const unsigned tno = NRB <= 1 ? rel / nsets : rel;
         const unsigned i = tno * TS + tx;
         const V *links = static_cast<const V *>(G.links);
         if (NRB > 1) {
@@ -145,69 +208,69 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
             }
             __syncthreads();
         }
-        const int passes = NRB <= 1 ? 1 : (G.nrhs + NRB - 1) / NRB;
+        const int passes = NRB <= 1 ? 1 : (G.nrhs + NRB * RPT - 1) / (NRB * RPT);
         for (int q = 0; q < passes; ++q) {
-            const int r = NRB <= 1 ? int(rel % unsigned(G.nrhs)) : q * NRB + int(ty);
-            const BSys *S = r < G.nrhs ? &sys[G.sys0 + r] : nullptr;
-            const bool active = S && !gated(S->s, gate);
-            double nrm = 0.0;
-            if (active && i < G.g.vh) {
-                Spinor<R> acc, o;
+            // right-hand sides r0 + j * step, j < RPT
+            const int r0 = NRB <= 1 ? int(rel % nsets) * RPT : q * NRB * RPT + int(ty);
+            const int step = NRB <= 1 ? 1 : NRB;
+            const BSys *S[RPT];
+            bool act[RPT], any = false;
+            double nrm[RPT];
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                const int r = r0 + j * step;
+                S[j] = r < G.nrhs ? &sys[G.sys0 + r] : nullptr;
+                act[j] = S[j] && !gated(S[j]->s, gate);
+                any = any || act[j];
+                nrm[j] = 0.0;
+            }
+            if (any && i < G.g.vh) {
                 Nbrs n;
                 neighbours(G.g, parity, i, n);
-                if (NRB > 1) {
-                    StagedLinks<P, RECON> src{tile, TS, tx};
-                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
+                if constexpr (RPT == 1) {
+                    Spinor<R> acc;
+                    if (NRB > 1) {
+                        StagedLinks<P, RECON> src{tile, TS, tx};
+                        hop_site_src<P, false>(G.g, n, src, S[0]->f[rin], acc);
+                    } else {
+                        GlobalLinks<P, RECON, NRB == 1> src{links, G.g.vh, i, parity};
+                        hop_site_src<P, false>(G.g, n, src, S[0]->f[rin], acc);
+                    }
+                    nrm[0] = batch_site_out<P, MODE>(S[0], G.g.vh, i, acc, k, rout, rx);
                 } else {
-                    GlobalLinks<P, RECON, NRB == 1> src{links, G.g.vh, i, parity};
-                    hop_site_src<P, false>(G.g, n, src, S->f[rin], acc);
-                }
-                if (rx >= 0) {
-                    Spinor<R> xs;
-                    SpinorIO<P>::load(S->f[rx], G.g.vh, i, xs);
-                    epilogue(k, acc, &xs, o);
-                } else {
-                    epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
-                }
-                if (MODE == BH_UPDATE) {
-                    constexpr int PY = P == F16 ? F32 : P;
-                    using RY = typename SpinorIO<PY>::R;
-                    const double alpha = S->s->alpha;
-                    Spinor<R> pv, rv;
-                    Spinor<RY> yv;
-                    SpinorIO<P>::load(S->f[R_P], G.g.vh, i, pv);
-                    SpinorIO<P>::load(S->f[R_R], G.g.vh, i, rv);
-                    SpinorIO<PY>::load(S->f[R_Y], G.g.vh, i, yv);
-                    const R a = to_R<R>(alpha);
-                    const RY ay = to_R<RY>(alpha);
-#pragma unroll
-                    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            yv[sp][c].re += ay * RY(pv[sp][c].re);
-                            yv[sp][c].im += ay * RY(pv[sp][c].im);
-                            rv[sp][c].re -= a * o[sp][c].re;
-                            rv[sp][c].im -= a * o[sp][c].im;
-                        }
-                    SpinorIO<PY>::store(S->f[R_Y], G.g.vh, i, yv);
-                    SpinorIO<P>::store(S->f[R_R], G.g.vh, i, rv);
-                    nrm = norm2(rv);
-                } else {
-                    SpinorIO<P>::store(S->f[rout], G.g.vh, i, o);
-                    if (MODE == BH_NORM) nrm = norm2(o);
+                    // an inactive partner reads the active one's input; its result is dropped
+                    const void *in0 = act[0] ? S[0]->f[rin] : S[1]->f[rin];
+                    const void *in1 = act[1] ? S[1]->f[rin] : in0;
+                    Spinor<R> acc0, acc1;
+                    if (NRB > 1) {
+                        StagedLinks<P, RECON> src{tile, TS, tx};
+                        hop_site_src_pair<P, false>(G.g, n, src, in0, in1, acc0, acc1);
+                    } else {
+                        GlobalLinks<P, RECON, NRB == 1> src{links, G.g.vh, i, parity};
+                        hop_site_src_pair<P, false>(G.g, n, src, in0, in1, acc0, acc1);
+                    }
+                    if (act[0]) nrm[0] = batch_site_out<P, MODE>(S[0], G.g.vh, i, acc0, k, rout, rx);
+                    if (act[1]) nrm[1] = batch_site_out<P, MODE>(S[1], G.g.vh, i, acc1, k, rout, rx);
                 }
             }
             if (MODE != BH_PLAIN) {
                 // one partial per (system, tile): each warp sums its lanes, then the
                 // TS / 32 warps of each right-hand side are added in order
                 static_assert(TS % 32 == 0, "a warp must not span two right-hand sides");
-                const double ws = warp_sum(nrm);
-                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const double ws = warp_sum(nrm[j]);
+                    if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = ws;
+                }
                 __syncthreads();
-                if (tx == 0 && active) {
-                    double sum = 0.0;
-                    for (int w = 0; w < TS / 32; ++w) sum += red[(ty * TS) / 32 + w];
-                    S->partials[tno] = sum;
+                if (tx == 0) {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) {
+                        if (!act[j]) continue;
+                        double sum = 0.0;
+                        for (int w = 0; w < TS / 32; ++w) sum += red[j][(ty * TS) / 32 + w];
+                        S[j]->partials[tno] = sum;
+                    }
                 }
                 __syncthreads();
             }
@@ -215,37 +278,50 @@ __global__ void __launch_bounds__(BT) k_batch_hop(const BGroup *__restrict__ gro
     }
 }
 
-template <int P, int RECON, int NRB, bool WITH_NORM = true>
+template <int P, int RECON, int NRB, int RPT, bool WITH_NORM = true>
 inline cudaError_t hop_nrb(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, int mode,
                     int gate, cudaStream_t st)
 {
     if (mode != BH_PLAIN) {
         if constexpr (WITH_NORM) {
             if (mode == BH_NORM)
-                k_batch_hop<P, RECON, NRB, BH_NORM><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+                k_batch_hop<P, RECON, NRB, BH_NORM, RPT><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
             else
-                k_batch_hop<P, RECON, NRB, BH_UPDATE><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+                k_batch_hop<P, RECON, NRB, BH_UPDATE, RPT><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
         } else {
             return cudaErrorInvalidValue;
         }
     } else {
-        k_batch_hop<P, RECON, NRB, BH_PLAIN><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
+        k_batch_hop<P, RECON, NRB, BH_PLAIN, RPT><<<t.grid, BT, 0, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin, rout, rx, k, gate);
     }
     return cudaGetLastError();
 }
+
+// Two right-hand sides per thread are built for the memory-latency-bound
+// formats only (FP32, FP16); the FP64 formats are bound by arithmetic.
+template <int P> constexpr bool has_rpt2() { return P == F32 || P == F16; }
 
 template <int P, int RECON, bool WITH_NORM = true>
 inline cudaError_t hop_pr(const HopTable &t, const BSys *sys, int parity, int rin, int rout, int rx, const Coef &k, int mode,
                    int gate, cudaStream_t st)
 {
     switch (t.nrb) {
-    case 0: return hop_nrb<P, RECON, 0, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
-    case 1: return hop_nrb<P, RECON, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case 0: return hop_nrb<P, RECON, 0, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case 1: return hop_nrb<P, RECON, 1, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
     case 2:
         // 8-byte-per-real tiles of 64 sites would exceed 48 KB of static shared memory
-        if constexpr (P != F64 && P != F64X) return hop_nrb<P, RECON, 2, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+        if constexpr (P != F64 && P != F64X) return hop_nrb<P, RECON, 2, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
         return cudaErrorInvalidValue;
-    case 4: return hop_nrb<P, RECON, 4, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case 4: return hop_nrb<P, RECON, 4, 1, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+    case 10:
+        if constexpr (has_rpt2<P>()) return hop_nrb<P, RECON, 0, 2, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+        return cudaErrorInvalidValue;
+    case 12:
+        if constexpr (has_rpt2<P>()) return hop_nrb<P, RECON, 2, 2, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+        return cudaErrorInvalidValue;
+    case 14:
+        if constexpr (has_rpt2<P>()) return hop_nrb<P, RECON, 4, 2, WITH_NORM>(t, sys, parity, rin, rout, rx, k, mode, gate, st);
+        return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }

@@ -998,6 +998,65 @@ TM_HD void hop_site_src(const Geom &g, const Nbrs &n, const Src &src, const void
     }
 }
 
+// The hop of one site for two input fields at once (two right-hand sides on
+// one lattice): each link is loaded once and applied to both, and the two
+// fields' neighbour loads are independent, so a thread has twice the loads
+// in flight (per-hop form; for the storage formats whose hop is bound by
+// memory latency, not by FP64 arithmetic).
+template <int P, bool DAG, int MU, class Src>
+TM_HD void hop_dir2(const Geom &g, const Nbrs &n, const Src &src, const void *in0, const void *in1,
+                    Spinor<typename SpinorIO<P>::R> &a0, Spinor<typename SpinorIO<P>::R> &a1)
+{
+    using R = typename SpinorIO<P>::R;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    {
+        Half<R> h0, h1, r;
+        Link<R> u;
+        R w0 = load_project<P, MU, SF>(in0, g.vh, n.fwd[MU], h0);
+        R w1 = load_project<P, MU, SF>(in1, g.vh, n.fwd[MU], h1);
+        src.template fwd<MU>(n, u);
+        if (n.wf[MU] && g.anti[MU]) {
+            w0 = -w0;
+            w1 = -w1;
+        }
+        link_mul<false>(u, h0, r);
+        accumulate<MU, SF>(r, w0, a0);
+        link_mul<false>(u, h1, r);
+        accumulate<MU, SF>(r, w1, a1);
+    }
+    {
+        Half<R> h0, h1, r;
+        Link<R> u;
+        R w0 = load_project<P, MU, SB>(in0, g.vh, n.bwd[MU], h0);
+        R w1 = load_project<P, MU, SB>(in1, g.vh, n.bwd[MU], h1);
+        src.template bwd<MU>(n, u);
+        if (n.wb[MU] && g.anti[MU]) {
+            w0 = -w0;
+            w1 = -w1;
+        }
+        link_mul<true>(u, h0, r);
+        accumulate<MU, SB>(r, w0, a0);
+        link_mul<true>(u, h1, r);
+        accumulate<MU, SB>(r, w1, a1);
+    }
+}
+
+template <int P, bool DAG, class Src>
+TM_HD void hop_site_src_pair(const Geom &g, const Nbrs &n, const Src &src, const void *in0, const void *in1,
+                             Spinor<typename SpinorIO<P>::R> &a0, Spinor<typename SpinorIO<P>::R> &a1)
+{
+    using R = typename SpinorIO<P>::R;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a0[s][c] = a1[s][c] = {R(0), R(0)};
+    hop_dir2<P, DAG, 0>(g, n, src, in0, in1, a0, a1);
+    hop_dir2<P, DAG, 1>(g, n, src, in0, in1, a0, a1);
+    hop_dir2<P, DAG, 2>(g, n, src, in0, in1, a0, a1);
+    hop_dir2<P, DAG, 3>(g, n, src, in0, in1, a0, a1);
+}
+
 // The hop at output site i of parity p with links read from the packed gauge field.
 template <int P, int RECON, bool DAG>
 TM_HD void hop_site(const Geom &g, int p, unsigned i, const typename LinkIO<P, RECON>::V *links, const void *in,

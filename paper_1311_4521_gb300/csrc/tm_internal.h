@@ -24,6 +24,8 @@ struct tm_ctx {
     void *red = nullptr;             // partial sums of tm_spinor_dot (grow-only)
     size_t red_bytes = 0;
     int autotune = 1;                // time launch configurations on first use
+    int batch_code = -1;             // forced batched-hop configuration (tm_ctx_set_batch_config), -1 = tuned
+    unsigned batch_cap = 0;          // and its persistent CTA cap (0: one CTA per work item)
     std::map<std::string, std::pair<int, unsigned>> tuned;  // batched hop: key -> (pass width, CTA cap)
     std::map<std::string, float> tuned_ms;                  // and the winner's time for 3 launches
     std::map<std::string, std::string> tuned_maps;          // single-lattice hop: key -> chosen map (tm_gauge_tune)

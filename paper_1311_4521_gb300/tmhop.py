@@ -88,6 +88,7 @@ def _load() -> ctypes.CDLL:
         "tm_ctx_device_bytes": ([P], S),
         "tm_slab_face_bytes": ([P], S),
         "tm_ctx_set_tune_cache": ([P, ctypes.c_char_p], I),
+        "tm_ctx_set_batch_config": ([P, I, ctypes.c_uint], I),
         "tm_gauge_tune": ([P, P, P], I),
         "tm_gauge_set_map": ([P, P, ctypes.c_char_p], I),
         "tm_gauge_map": ([P, ctypes.c_char_p, S], S),
@@ -298,6 +299,11 @@ def tm_scale_complex(ctx, n, z_dev, alpha_dev, c, stream=None):
 def tm_ctx_set_tune_cache(ctx, path) -> None:
     """Autotune cache file of the context (None: no file)."""
     _check(ctx, lib.tm_ctx_set_tune_cache(ctx, None if path is None else str(path).encode()))
+
+
+def tm_ctx_set_batch_config(ctx, code: int, cap: int = 0) -> None:
+    """Fixes the batched hop's configuration (code -1: back to the autotuner)."""
+    _check(ctx, lib.tm_ctx_set_batch_config(ctx, int(code), int(cap)))
 
 
 def tm_gauge_tune(ctx, U, stream=None) -> None:

@@ -189,3 +189,52 @@ def test_batching_workload_full_size(ctx):
         assert oracle_relres(dims, U, xs_, psi, 0.1394, 0.0015) <= 1.05e-10, (dims, inf)
     for g in gh + gl:
         g.close()
+
+
+CODES = {"f64": [0, 1, 4], "f32": [0, 1, 2, 4, 10, 12, 14], "f16": [0, 1, 2, 4, 10, 12, 14]}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_every_batch_configuration(ctx, prec):
+    """Every configuration of the batched hop (pass width, right-hand sides
+    per thread, CTA cap), forced instead of tuned, against the oracle, with
+    an odd number of right-hand sides (a thread pair with one member idle)
+    and a second lattice; and the batched solver (the norm and update modes
+    of the hop) in the reduced-precision formats."""
+    from paper_1311_4521_gb300 import tmhop
+    spec = [((8, 8, 8, 8), 5), ((6, 4, 2, 10), 1)]
+    lats, systems = make_batch(spec, seed0=500)
+    gauges = [ctx.gauge(d, U, prec, RECON[prec]) for d, U in lats]
+    ins = [ctx.pack(psi, prec) for _, psi in systems]
+    want = [O.Qtm(lats[li][0], lats[li][1], psi, 0.1394, 0.0015) for li, psi in systems]
+    try:
+        for code in CODES[prec]:
+            for cap in (0, 7):
+                tmhop.tm_ctx_set_batch_config(ctx.handle, code, cap)
+                outs = [ctx.empty(psi.shape[0], prec) for _, psi in systems]
+                for o in outs:
+                    o.fill_(0xFF)
+                ctx.Qtm_batch([gauges[li] for li, _ in systems], outs, ins, 0.1394, 0.0015)
+                for (li, psi), out, w in zip(systems, outs, want):
+                    got = ctx.unpack(out, psi.shape[0], prec).cpu().numpy()
+                    assert np.all(np.isfinite(got)) and rel(got, w) < TOL[prec], (code, cap)
+            if prec == "f64":
+                continue
+            gh = [ctx.gauge(d, U, "f64", 18) for d, U in lats]
+            xs = [ctx.empty(psi.shape[0], "f64").zero_() for _, psi in systems]
+            bs = [ctx.pack(psi, "f64") for _, psi in systems]
+            st, infos = ctx.cg_batch([gh[li] for li, _ in systems], xs, bs, 0.1394, 0.0015, 1e-10, 20000,
+                                     [gauges[li] for li, _ in systems])
+            assert st == tmhop.TM_OK, (code, infos)
+            for (li, psi), x in zip(systems, xs):
+                dims, U = lats[li]
+                assert oracle_relres(dims, U, ctx.unpack(x, psi.shape[0], "f64").cpu().numpy(), psi,
+                                     0.1394, 0.0015) <= 1.05e-10, code
+            for g in gh:
+                g.close()
+        with pytest.raises(tmhop.TmError):
+            tmhop.tm_ctx_set_batch_config(ctx.handle, 3, 0)
+    finally:
+        tmhop.tm_ctx_set_batch_config(ctx.handle, -1, 0)
+        for g in gauges:
+            g.close()
