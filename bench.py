@@ -765,7 +765,11 @@ def batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U32=None) -> dict
                 "ms_batched": round(mb, 4), "ms_one_call_each": round(ms, 4), "speedup": round(ms / mb, 2)}
 
     out["qtm_8_uneven_lattices"] = many_lattices(UNEVEN, F.SEED_BATCH_LATTICE)
+    out["qtm_8_uneven_lattices"]["note"] = (
+        "every lattice but 12^3x24 has >= 65,536 even sites (>= 430 per SM) and fills the GPU alone: "
+        "one persistent launch for all eight saves launches, not time")
     out["qtm_64_lattices_8x8x8x8"] = many_lattices([(8, 8, 8, 8)] * 64, F.SEED_BATCH_LATTICE + 1000)
+    out["qtm_64_lattices_8x8x8x8"]["note"] = "1,024 even sites per lattice, less than one CTA per SM: batching pays"
     for g in gh + gl:
         g.close()
     return out
