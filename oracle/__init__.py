@@ -57,6 +57,8 @@ def _bind(lib):
     lib.oracle_twist_inv.argtypes = [L, D, P, P]
     lib.oracle_Qtm.argtypes = [I4, I4, P, D, D, P, P]
     lib.oracle_Qtm_dagger.argtypes = [I4, I4, P, D, D, P, P]
+    lib.oracle_Qnd.argtypes = [I4, I4, P, D, D, D, P, P, P, P]
+    lib.oracle_Qnd.restype = ctypes.c_int
     lib.oracle_cg_QdagQ.argtypes = [I4, I4, P, D, D, P, P, D, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(D)]
     lib.oracle_cg_QdagQ.restype = ctypes.c_int
@@ -157,6 +159,18 @@ def Qtm(dims, U, psi_e, kappa, mu, bc=ANTIPERIODIC_T, dagger=False):
     f = _load().oracle_Qtm_dagger if dagger else _load().oracle_Qtm
     f(_i4(dims), _i4(bc), _p(U), float(kappa), float(mu), _p(psi_e), _p(out))
     return out
+
+
+def Qnd(dims, U, psi_s, psi_c, kappa, mu_sigma, mu_delta, bc=ANTIPERIODIC_T):
+    """The non-degenerate twisted doublet Q_nd on an even-site doublet (psi_s, psi_c);
+    returns (out_s, out_c).  Raises ValueError if M_oo is singular."""
+    U, psi_s, psi_c = _c(U), _c(psi_s), _c(psi_c)
+    out_s, out_c = np.empty_like(psi_s), np.empty_like(psi_c)
+    ok = _load().oracle_Qnd(_i4(dims), _i4(bc), _p(U), float(kappa), float(mu_sigma), float(mu_delta),
+                            _p(psi_s), _p(psi_c), _p(out_s), _p(out_c))
+    if not ok:
+        raise ValueError("Qnd: the site-local matrix M_oo is singular")
+    return out_s, out_c
 
 
 def cg_QdagQ(dims, U, b_e, kappa, mu, tol=1e-10, maxiter=10000, x0=None, bc=ANTIPERIODIC_T):

@@ -38,7 +38,8 @@
  * the free-field plane-wave closed form; gauge covariance; gamma5
  * hermiticity; the literal adjoint against the dense conjugate transpose;
  * CG against a dense solve; the force against finite differences of the
- * action.
+ * action; the non-degenerate doublet against its dense Schur complement and
+ * its flavour-diagonal (mu_delta = 0) limit.
  */
 #include <complex.h>
 #include <math.h>
@@ -406,6 +407,129 @@ void oracle_Qtm_dagger(const int dims[4], const int bc[4], const double complex 
     oracle_twist(Vh, -mut, g_e, out_e);                            /* M_ee^dag */
     for (long k = 0; k < Vh * SPINOR; ++k) out_e[k] -= v_e[k];
     free(g_e); free(t_o); free(u_o); free(v_e);
+}
+
+/* ------------------------------------------------------------------ */
+/* Non-degenerate twisted-mass doublet                                  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The mass-non-degenerate twisted doublet (Frezzotti and Rossi's
+ * strange-charm doublet, one of the operators of the tmLQCD suite the
+ * paper's introduction lists) acts on two flavours (psi_s, psi_c):
+ *
+ *   M_nd = (1 - kappa Dhop) x 1_f + i mubar gamma5 x tau3 - epsbar 1 x tau1,
+ *   mubar = 2 kappa mu_sigma, epsbar = 2 kappa mu_delta,
+ *
+ * with Dhop acting on each flavour alone.  Even-odd: A = M_ee = M_oo =
+ * 1 + i mubar gamma5 tau3 - epsbar tau1 (site-local, spin x flavour),
+ * M_eo = -kappa H_eo, M_oe = -kappa H_oe, and
+ *
+ *   Q_nd = gamma5 (M_ee - M_eo M_oo^-1 M_oe)     on even doublets.
+ *
+ * Here A is built as an explicit 8x8 matrix (spin x flavour, colour is
+ * untouched) and M_oo^-1 is its numerical inverse (Gauss-Jordan with
+ * partial pivoting), not a closed form.  Layout of a doublet field: flavour
+ * s in one array, c in another, each [i_eo][spin][colour].
+ */
+
+/* A = 1 + i mubar gamma5 tau3 - epsbar tau1, index f*4 + spin. */
+static void nd_site_matrix(double mubar, double epsbar, cplx A[8][8])
+{
+    ensure_gammas();
+    const double tau1[2][2] = {{0, 1}, {1, 0}}, tau3[2][2] = {{1, 0}, {0, -1}};
+    for (int f = 0; f < 2; ++f)
+        for (int a = 0; a < 4; ++a)
+            for (int g = 0; g < 2; ++g)
+                for (int b = 0; b < 4; ++b)
+                    A[f * 4 + a][g * 4 + b] = (f == g && a == b ? 1.0 : 0.0) + I * mubar * G[4][a][b] * tau3[f][g] -
+                                              epsbar * (a == b ? 1.0 : 0.0) * tau1[f][g];
+}
+
+/* B = A^-1 by Gauss-Jordan elimination with partial pivoting; returns 0 if singular. */
+static int invert8(cplx A[8][8], cplx B[8][8])
+{
+    cplx M[8][16];
+    for (int r = 0; r < 8; ++r)
+        for (int c = 0; c < 16; ++c) M[r][c] = c < 8 ? A[r][c] : (c - 8 == r ? 1.0 : 0.0);
+    for (int c = 0; c < 8; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 8; ++r)
+            if (cabs(M[r][c]) > cabs(M[piv][c])) piv = r;
+        if (cabs(M[piv][c]) < 1e-300) return 0;
+        for (int k = 0; k < 16; ++k) {
+            cplx t = M[c][k];
+            M[c][k] = M[piv][k];
+            M[piv][k] = t;
+        }
+        cplx d = M[c][c];
+        for (int k = 0; k < 16; ++k) M[c][k] /= d;
+        for (int r = 0; r < 8; ++r) {
+            if (r == c) continue;
+            cplx f = M[r][c];
+            for (int k = 0; k < 16; ++k) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int r = 0; r < 8; ++r)
+        for (int c = 0; c < 8; ++c) B[r][c] = M[r][c + 8];
+    return 1;
+}
+
+/* (out_s, out_c) = W (in_s, in_c) at every site for a site-local 8x8 W. */
+static void nd_apply(long n, cplx W[8][8], const cplx *in_s, const cplx *in_c, cplx *out_s, cplx *out_c)
+{
+    for (long i = 0; i < n; ++i)
+        for (int col = 0; col < NCOL; ++col)
+            for (int fa = 0; fa < 8; ++fa) {
+                cplx acc = 0;
+                for (int gb = 0; gb < 8; ++gb) {
+                    const cplx *src = gb < 4 ? in_s : in_c;
+                    acc += W[fa][gb] * src[i * SPINOR + (gb % 4) * NCOL + col];
+                }
+                cplx *dst = fa < 4 ? out_s : out_c;
+                dst[i * SPINOR + (fa % 4) * NCOL + col] = acc;
+            }
+}
+
+/* (out_s, out_c) = Q_nd (in_s, in_c) on even sites; returns 0 if M_oo is singular. */
+int oracle_Qnd(const int dims[4], const int bc[4], const double complex *U, double kappa, double mu_sigma,
+               double mu_delta, const double complex *in_s, const double complex *in_c, double complex *out_s,
+               double complex *out_c)
+{
+    long Vh = volume(dims) / 2;
+    cplx A[8][8], Ainv[8][8];
+    nd_site_matrix(2.0 * kappa * mu_sigma, 2.0 * kappa * mu_delta, A);
+    if (!invert8(A, Ainv)) return 0;
+    long n = Vh * SPINOR;
+    cplx *t[2], *u[2], *v[2], *w[2];
+    for (int f = 0; f < 2; ++f) {
+        t[f] = malloc(sizeof(cplx) * n);
+        u[f] = malloc(sizeof(cplx) * n);
+        v[f] = malloc(sizeof(cplx) * n);
+        w[f] = malloc(sizeof(cplx) * n);
+    }
+    const cplx *in[2] = {in_s, in_c};
+    for (int f = 0; f < 2; ++f) {
+        oracle_hopping(dims, bc, U, 1, in[f], t[f], 0);             /* H_oe in */
+        for (long k = 0; k < n; ++k) t[f][k] *= -kappa;              /* M_oe in */
+    }
+    nd_apply(Vh, Ainv, t[0], t[1], u[0], u[1]);                      /* M_oo^-1 M_oe in */
+    for (int f = 0; f < 2; ++f) {
+        oracle_hopping(dims, bc, U, 0, u[f], v[f], 0);              /* H_eo ... */
+        for (long k = 0; k < n; ++k) v[f][k] *= -kappa;              /* M_eo M_oo^-1 M_oe in */
+    }
+    nd_apply(Vh, A, in_s, in_c, w[0], w[1]);                         /* M_ee in */
+    for (int f = 0; f < 2; ++f)
+        for (long k = 0; k < n; ++k) w[f][k] -= v[f][k];
+    oracle_gamma5(Vh, w[0], out_s);
+    oracle_gamma5(Vh, w[1], out_c);
+    for (int f = 0; f < 2; ++f) {
+        free(t[f]);
+        free(u[f]);
+        free(v[f]);
+        free(w[f]);
+    }
+    return 1;
 }
 
 /* ------------------------------------------------------------------ */

@@ -1,7 +1,8 @@
 """The pins catch plausible mistakes: each case plants one mistake in a copy
 of the oracle's C source (a flipped projector sign, U where U^dag belongs,
 the backward link taken at the wrong site, the boundary sign dropped, the
-sign of M_oo^-1 or of kappa flipped, one force term with the wrong sign),
+sign of M_oo^-1 or of kappa flipped, one force term with the wrong sign,
+the doublet's flavour splitting or twist or M_oo^-1 wrong),
 builds it into a scratch library, points the oracle at it and requires at
 least one of the oracle pins to fail.  The unmodified oracle passes the same
 pins.  CPU only; the planted mistakes live in temporary files only."""
@@ -13,6 +14,7 @@ import pytest
 
 import oracle as O
 
+import test_oracle_nd_pins as nd_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(O.__file__), "tm_oracle.c")
@@ -28,6 +30,11 @@ MUTANTS = [
     ("M_oo^-1 with the wrong twist sign", "oracle_twist_inv(Vh, mut, t_o, u_o);", "oracle_twist_inv(Vh, -mut, t_o, u_o);"),
     ("minus sign of M_oe = -kappa H_oe dropped", "t_o[k] *= -kappa;", "t_o[k] *= kappa;"),
     ("force: second term with the wrong sign", "creal(term1 + term2)", "creal(term1 - term2)"),
+    ("doublet: sign of the flavour splitting", "epsbar * (a == b ? 1.0 : 0.0) * tau1[f][g]",
+     "-epsbar * (a == b ? 1.0 : 0.0) * tau1[f][g]"),
+    ("doublet: twist without tau3", "I * mubar * G[4][a][b] * tau3[f][g]", "I * mubar * G[4][a][b] * (f == g ? 1.0 : 0.0)"),
+    ("doublet: M_oo instead of M_oo^-1", "nd_apply(Vh, Ainv, t[0], t[1], u[0], u[1]);",
+     "nd_apply(Vh, A, t[0], t[1], u[0], u[1]);"),
 ]
 
 
@@ -43,6 +50,9 @@ def run_pins():
         (pins.test_special_cases_reduce, ()),
         (pins.test_force_matches_finite_differences_of_dense_action, ((2, 2, 2, 2),)),
         (pins.test_force_gauge_covariance, ()),
+        (nd_pins.test_Qnd_matches_dense_schur_complement, ((2, 2, 2, 2),)),
+        (nd_pins.test_Qnd_without_splitting_is_two_degenerate_operators, ()),
+        (nd_pins.test_Qnd_adjoint_is_Qnd_with_minus_mu_sigma, ()),
     ]
     failed = []
     for fn, args in cases:
