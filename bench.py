@@ -409,6 +409,11 @@ def gpu_arm(args) -> None:
             gp.close()
             del sp, dp
 
+    # ---- the non-degenerate twisted doublet (two flavours, links loaded once for both)
+    nd = None
+    if not args.no_table:
+        nd = nd_section(args, ctx, tmhop, torch, F, U, DIMS, vh, hbm_peak, allmax)
+
     # ---- CG on Q^dag Q to true relative residual 1e-10: FP64 vs mixed precision
     cg = None
     cg_host = None
@@ -471,13 +476,57 @@ def gpu_arm(args) -> None:
                               f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"),
             "gflops": round(gflops, 2), "roofline": roofline, "fp64_probe": probe, "hbm_peak_gbs": hbm_peak,
             "hbm_peak_source": hbm_src,
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "nd_doublet": nd, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def nd_section(args, ctx, tmhop, torch, F, U, dims, vh, hbm_peak, allmax) -> dict:
+    """The non-degenerate twisted doublet Q_nd (mu_sigma = 0.0015, mu_delta =
+    0.0018) on the workload lattice in FP64-18, FP32-12 and FP16-12: ms per
+    application and launch B's algorithmic GB/s.  Per even site, launch A
+    reads two flavours' spinors and the 8 links once and writes two
+    flavours; launch B also re-reads both even inputs."""
+    psi_s = F.gaussian_spinor(vh, F.SEED_PROD_32, 1)
+    psi_c = F.gaussian_spinor(vh, F.SEED_PROD_32, 2)
+    out = {"mu_sigma": 0.0015, "mu_delta": 0.0018}
+    stream = torch.cuda.current_stream()
+    for prec, recon in (("f64", 18), ("f32", 12), ("f16", 12)):
+        g = ctx.gauge(dims, U, prec, recon)
+        ins = [ctx.pack(psi_s, prec), ctx.pack(psi_c, prec)]
+        outs = [ctx.empty(vh, prec), ctx.empty(vh, prec)]
+        n = max(3, min(args.steps, args.table_steps))
+        for _ in range(args.warmup):
+            ctx.Qnd(g, outs, ins, KAPPA, 0.0015, 0.0018)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+        for trio in ev:
+            for e in trio:
+                e.record(stream)
+        torch.cuda.synchronize()
+        for k in range(n):
+            tmhop.tm_ctx_trace(ctx.handle, ev[k])
+            ctx.Qnd(g, outs, ins, KAPPA, 0.0015, 0.0018)
+        tmhop.tm_ctx_trace(ctx.handle, None)
+        torch.cuda.synchronize()
+        total = allmax(sum(e[0].elapsed_time(e[2]) for e in ev) / n)
+        kb = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+        sp = 24 * REAL[prec] + (4 if prec == "f16" else 0)      # one spinor per site
+        links = 8 * recon * REAL[prec]
+        a_bytes, b_bytes = 2 * (sp + sp) + links, 2 * (sp + sp + sp) + links
+        gbs = vh * b_bytes / (kb * 1e-3) / 1e9
+        out[f"{prec}-{recon}"] = {"ms_per_qnd": round(total, 4), "kernel_b_ms": round(kb, 4),
+                                  "GBps": round(vh * (a_bytes + b_bytes) / (total * 1e-3) / 1e9, 1),
+                                  "kernel_b_GBps": round(gbs, 1), "kernel_b_hbm_frac": round(gbs / hbm_peak, 4),
+                                  "gflops": round(vh * 2 * (2 * HOP_FLOPS) / (total * 1e-3) / 1e9, 1)}
+        g.close()
+        del ins, outs
+    out["note"] = ("bytes per even site: launch A 2 x (in + out) + 8 links, launch B 2 x (in + out + x) + 8 links; "
+                   "flops counted: the two flavours' hops (2 x 2 x 1320)")
+    return out
 
 
 def cg_section(args, ctx, tmhop, torch, F, allmax, barrier, keep_host=False):

@@ -203,6 +203,25 @@ tm_status tm_hopping_eo(tm_ctx *ctx, const tm_gauge *U, void *out_dev, const voi
 tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in_e_dev, double kappa, double mu,
                  int sign, void *stream);
 
+/* The non-degenerate twisted-mass doublet (the mass-split flavour doublet
+ * of the tmLQCD suite, whose operators the paper's introduction lists):
+ * on an even-site doublet (in_s, in_c),
+ *   (out_s, out_c) = Q_nd (in_s, in_c),  Q_nd = gamma5 (A - kappa^2 H_eo A^-1 H_oe),
+ *   A = 1 + i mubar gamma5 tau3 - epsbar tau1 (site-local, spin x flavour),
+ *   mubar = 2 kappa sign mu_sigma, epsbar = 2 kappa mu_delta,
+ * the hops acting on each flavour alone.  sign = -1 gives Q_nd(-mu_sigma,
+ * mu_delta) = Q_nd(mu_sigma, mu_delta)^dagger; mu_delta = 0 gives
+ * (Q_tm(mu) in_s, Q_tm(-mu) in_c).  Both flavours of a site are hopped by
+ * one thread with one load of each link; A^-1 = (1 - i mubar gamma5 tau3 +
+ * epsbar tau1) / (1 + mubar^2 - epsbar^2) and A are fused into the two
+ * launches like tm_Qtm's site-local factors.  Fields are packed in U's
+ * precision (TM_F64, TM_F32 or TM_F16; TM_F64X: TM_ERR_UNSUPPORTED); the
+ * outputs must differ from each other and from the inputs; a singular A
+ * (epsbar^2 = 1 + mubar^2) gives TM_ERR_ARG.  Two odd temporaries live in
+ * ctx's scratch.  Traced like tm_Qtm (events 0, 1, 2). */
+tm_status tm_Qnd(tm_ctx *ctx, const tm_gauge *U, void *out_s_dev, void *out_c_dev, const void *in_s_dev,
+                 const void *in_c_dev, double kappa, double mu_sigma, double mu_delta, int sign, void *stream);
+
 /* ---- solver ------------------------------------------------------------- */
 
 /* Parameters of tm_cg_QdagQ. */

@@ -88,6 +88,7 @@ def _load() -> ctypes.CDLL:
         "tm_ctx_device_bytes": ([P], S),
         "tm_slab_face_bytes": ([P], S),
         "tm_ctx_set_tune_cache": ([P, ctypes.c_char_p], I),
+        "tm_Qnd": ([P, P, P, P, P, P, D, D, D, I, P], I),
         "tm_ctx_set_batch_config": ([P, I, ctypes.c_uint], I),
         "tm_gauge_tune": ([P, P, P], I),
         "tm_gauge_set_map": ([P, P, ctypes.c_char_p], I),
@@ -296,6 +297,12 @@ def tm_scale_complex(ctx, n, z_dev, alpha_dev, c, stream=None):
     _check(ctx, lib.tm_scale_complex(ctx, int(n), _ptr(z_dev), _ptr(alpha_dev), float(c), _stream(stream)))
 
 
+def tm_Qnd(ctx, U, out_s, out_c, in_s, in_c, kappa, mu_sigma, mu_delta, sign=1, stream=None):
+    """The non-degenerate twisted doublet on packed even fields (see include/tmhop.h)."""
+    _check(ctx, lib.tm_Qnd(ctx, U, _ptr(out_s), _ptr(out_c), _ptr(in_s), _ptr(in_c), float(kappa), float(mu_sigma),
+                           float(mu_delta), int(sign), _stream(stream)))
+
+
 def tm_ctx_set_tune_cache(ctx, path) -> None:
     """Autotune cache file of the context (None: no file)."""
     _check(ctx, lib.tm_ctx_set_tune_cache(ctx, None if path is None else str(path).encode()))
@@ -448,6 +455,11 @@ class Context:
         F = torch.empty((4, V, 3, 3, 2), dtype=torch.float64, device=self.device)
         tm_force_ex(self.handle, U.handle, F, X_e, kappa, mu, mode, scheme)
         return torch.view_as_complex(F)
+
+    def Qnd(self, U: Gauge, outs, ins, kappa, mu_sigma, mu_delta, sign=1):
+        """(out_s, out_c) = Q_nd (in_s, in_c) on packed even fields."""
+        tm_Qnd(self.handle, U.handle, outs[0], outs[1], ins[0], ins[1], kappa, mu_sigma, mu_delta, sign)
+        return outs
 
     def Qtm_host(self, U: Gauge, outs, ins, kappa, mu, sign=1):
         """Q_tm on host tensors (complex128 [Vh, 4, 3], contiguous, on the CPU; pin them for overlap)."""
