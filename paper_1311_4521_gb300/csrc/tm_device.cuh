@@ -111,16 +111,49 @@ template <typename R> using Half = cpx<R>[2][3];
 template <typename R> using Link = cpx<R>[3][3];
 
 // ---------------------------------------------------------------- geometry
+// Division by a divisor fixed on the host: q = (umulhi(n, m) + n) >> s with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1, exact for every
+// n < 2^31 (the "round-up" method of Granlund and Montgomery, PLDI 1994).
+struct FastDiv {
+    unsigned d = 1, m = 0, s = 0;
+    FastDiv() = default;
+    explicit FastDiv(unsigned div) : d(div)
+    {
+        while ((1ull << s) < d) ++s;
+        m = unsigned(((1ull << 32) * ((1ull << s) - d)) / d + 1);
+    }
+    TM_HD unsigned div(unsigned n) const
+    {
+#if defined(__CUDA_ARCH__)
+        const unsigned hi = __umulhi(n, m);
+#else
+        const unsigned hi = unsigned((static_cast<unsigned long long>(n) * m) >> 32);
+#endif
+        return (hi + n) >> s;
+    }
+};
+
 // Extents and the even-odd strides.  A one-parity field stores site lex at
 // index lex/2; with Lx even, moving by one in y, z or t moves the index by
-// sy = Lx/2, sz = sy*Ly, st = sz*Lz.
+// sy = Lx/2, sz = sy*Ly, st = sz*Lz.  The divisions that recover a site's
+// coordinates from its index use the invariant-divisor form (three integer
+// operations instead of a division routine).
 struct Geom {
     int lx, ly, lz, lt;
     int hx;                 // lx / 2
     unsigned vh;            // sites per parity
     unsigned sy, sz, st;    // index strides of y, z, t
     int anti[4];            // 1 if a wrapping hop in direction mu (0=t,1=x,2=y,3=z) takes a minus sign
+    FastDiv dhx, dly, dlz;  // division by hx, ly, lz
 };
+
+// Fills the divisors of a geometry whose extents are set.
+inline void geom_set_divisors(Geom &g)
+{
+    g.dhx = FastDiv(unsigned(g.hx));
+    g.dly = FastDiv(unsigned(g.ly));
+    g.dlz = FastDiv(unsigned(g.lz));
+}
 
 // Neighbour indices (other parity) and wrap flags of output site i of parity p.
 struct Nbrs {
@@ -130,11 +163,9 @@ struct Nbrs {
 
 TM_HD void neighbours(const Geom &g, int p, unsigned i, Nbrs &n)
 {
-    unsigned xh = i % g.hx, r = i / g.hx;
-    unsigned y = r % g.ly;
-    r /= g.ly;
-    unsigned z = r % g.lz;
-    unsigned t = r / g.lz;
+    const unsigned q1 = g.dhx.div(i), xh = i - q1 * unsigned(g.hx);
+    const unsigned q2 = g.dly.div(q1), y = q1 - q2 * unsigned(g.ly);
+    const unsigned t = g.dlz.div(q2), z = q2 - t * unsigned(g.lz);
     unsigned x = 2 * xh + ((y + z + t + p) & 1);
     unsigned row = i - xh;
     // x
@@ -160,28 +191,6 @@ TM_HD void neighbours(const Geom &g, int p, unsigned i, Nbrs &n)
 }
 
 // ---------------------------------------------------------------- site maps
-// Division by a divisor fixed on the host: q = (umulhi(n, m) + n) >> s with
-// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1, exact for every
-// n < 2^31 (the "round-up" method of Granlund and Montgomery, PLDI 1994).
-struct FastDiv {
-    unsigned d = 1, m = 0, s = 0;
-    FastDiv() = default;
-    explicit FastDiv(unsigned div) : d(div)
-    {
-        while ((1ull << s) < d) ++s;
-        m = unsigned(((1ull << 32) * ((1ull << s) - d)) / d + 1);
-    }
-    TM_HD unsigned div(unsigned n) const
-    {
-#if defined(__CUDA_ARCH__)
-        const unsigned hi = __umulhi(n, m);
-#else
-        const unsigned hi = unsigned((static_cast<unsigned long long>(n) * m) >> 32);
-#endif
-        return (hi + n) >> s;
-    }
-};
-
 // Which output site (even-odd index) thread k of CTA b handles.  Linear:
 // site b * block + k (a CTA covers consecutive sites: with Lx/2 sites per
 // half-row, whole y rows at one z, t).  Tiled: a CTA covers a box of
@@ -1094,12 +1103,13 @@ struct Coef {
     TM_HD dd get(int k, dd) const { return dd{xh[k], xl[k]}; }
 };
 
-template <typename R> TM_HD void epilogue(const Coef &k, const Spinor<R> &hop, const Spinor<R> *x, Spinor<R> &out)
+// out_u = a_u hop_u + b_u x_u, out_l = a_l hop_l + b_l x_l per spin half;
+// with `unit` the hop term enters as +hop_u, -hop_l (no multiply).
+template <typename R>
+TM_HD void epilogue_with(cpx<R> au, cpx<R> al, cpx<R> bu, cpx<R> bl, bool unit, const Spinor<R> &hop,
+                         const Spinor<R> *x, Spinor<R> &out)
 {
-    const R z = R(0);
-    cpx<R> au = {k.get(0, z), k.get(1, z)}, al = {k.get(2, z), k.get(3, z)};
-    cpx<R> bu = {k.get(4, z), k.get(5, z)}, bl = {k.get(6, z), k.get(7, z)};
-    if (k.unit) {
+    if (unit) {
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -1119,6 +1129,25 @@ template <typename R> TM_HD void epilogue(const Coef &k, const Spinor<R> &hop, c
             if (x) v = cmadd(s < 2 ? bu : bl, (*x)[s][c], v);
             out[s][c] = v;
         }
+}
+
+template <typename R> TM_HD void epilogue(const Coef &k, const Spinor<R> &hop, const Spinor<R> *x, Spinor<R> &out)
+{
+    const R z = R(0);
+    cpx<R> au = {k.get(0, z), k.get(1, z)}, al = {k.get(2, z), k.get(3, z)};
+    cpx<R> bu = {k.get(4, z), k.get(5, z)}, bl = {k.get(6, z), k.get(7, z)};
+    epilogue_with(au, al, bu, bl, k.unit != 0, hop, x, out);
+}
+
+// The same with the x coefficients multiplied by xs: for half-precision
+// storage x is passed as its stored values and xs is its site norm, one
+// multiply per coefficient instead of one per component.
+TM_HD void epilogue(const Coef &k, const Spinor<float> &hop, const Spinor<float> *x, Spinor<float> &out, float xs)
+{
+    const float z = 0.f;
+    cpx<float> au = {k.get(0, z), k.get(1, z)}, al = {k.get(2, z), k.get(3, z)};
+    cpx<float> bu = {xs * k.get(4, z), xs * k.get(5, z)}, bl = {xs * k.get(6, z), xs * k.get(7, z)};
+    epilogue_with(au, al, bu, bl, k.unit != 0, hop, x, out);
 }
 
 }  // namespace twm

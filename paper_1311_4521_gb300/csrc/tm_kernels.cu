@@ -21,6 +21,7 @@ bool make_geom(const int dims[4], const int bc[4], Geom &g)
     g.sz = g.sy * unsigned(g.ly);
     g.st = g.sz * unsigned(g.lz);
     for (int m = 0; m < 4; ++m) g.anti[m] = bc ? (bc[m] < 0) : 0;
+    geom_set_divisors(g);
     return true;
 }
 
@@ -69,8 +70,13 @@ __global__ void __launch_bounds__(128, TM_HOP_MINB(P)) k_hop(Geom g, int p, cons
     hop_site<P, RECON, DAG>(g, p, i, links, in, acc);
     if (HASX) {
         Spinor<R> xs;
-        SpinorIO<P>::load(x, g.vh, i, xs);
-        epilogue(k, acc, &xs, o);
+        if constexpr (P == F16) {   // the re-read input's site norm folded into its coefficients
+            const R xn = SpinorIO<P>::load_raw(x, g.vh, i, xs);
+            epilogue(k, acc, &xs, o, xn);
+        } else {
+            SpinorIO<P>::load(x, g.vh, i, xs);
+            epilogue(k, acc, &xs, o);
+        }
     } else {
         epilogue(k, acc, static_cast<const Spinor<R> *>(nullptr), o);
     }

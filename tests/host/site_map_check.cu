@@ -1,7 +1,9 @@
-// Host-side check of the hop's site-to-thread maps (compiled with nvcc as a
+// Host-side check of the hop's index arithmetic (compiled with nvcc as a
 // host program; no GPU needed): every linear and box map of several lattice
-// shapes covers every even-odd site exactly once, and the division by
-// invariant integers used to number the boxes is exact.
+// shapes covers every even-odd site exactly once, the division by
+// invariant integers used for the boxes and the site coordinates is exact,
+// and every site's 8 neighbour indices and wrap flags agree with plain
+// coordinate arithmetic.
 #include <cstdio>
 #include <vector>
 
@@ -15,6 +17,7 @@ static Geom geom(int lx, int ly, int lz, int lt)
     g.lx = lx, g.ly = ly, g.lz = lz, g.lt = lt, g.hx = lx / 2;
     g.vh = unsigned(lx) * ly * lz * lt / 2;
     g.sy = g.hx, g.sz = g.sy * ly, g.st = g.sz * lz;
+    geom_set_divisors(g);
     return g;
 }
 
@@ -40,6 +43,37 @@ static int check_map(const Geom &g, const SiteMap &m, const char *what)
     return 0;
 }
 
+// neighbours() against coordinates decoded by plain division and the
+// neighbour indices recomputed from them, for both parities and all sites.
+static int check_neighbours(const Geom &g)
+{
+    for (int p = 0; p < 2; ++p)
+        for (unsigned i = 0; i < g.vh; ++i) {
+            Nbrs n;
+            neighbours(g, p, i, n);
+            const unsigned xh = i % g.hx, y = (i / g.hx) % g.ly, z = (i / g.hx / g.ly) % g.lz,
+                           t = i / g.hx / g.ly / g.lz;
+            const unsigned x = 2 * xh + ((y + z + t + p) & 1);
+            const int ext[4] = {g.lt, g.lx, g.ly, g.lz};
+            const unsigned c[4] = {t, x, y, z};
+            for (int mu = 0; mu < 4; ++mu)
+                for (int step = -1; step <= 1; step += 2) {
+                    unsigned cc[4] = {c[0], c[1], c[2], c[3]};
+                    cc[mu] = unsigned((int(cc[mu]) + step + ext[mu]) % ext[mu]);
+                    const unsigned lex = cc[1] + g.lx * (cc[2] + g.ly * (cc[3] + g.lz * cc[0]));
+                    const bool wrap = int(c[mu]) + step < 0 || int(c[mu]) + step >= ext[mu];
+                    const unsigned got = step > 0 ? n.fwd[mu] : n.bwd[mu];
+                    const bool gotw = step > 0 ? n.wf[mu] : n.wb[mu];
+                    if (got != lex / 2 || gotw != wrap) {
+                        printf("FAIL neighbours %dx%dx%dx%d p=%d i=%u mu=%d step=%d\n", g.lx, g.ly, g.lz, g.lt, p, i,
+                               mu, step);
+                        return 1;
+                    }
+                }
+        }
+    return 0;
+}
+
 int main()
 {
     int fails = 0, maps = 0;
@@ -61,6 +95,7 @@ int main()
                              {48, 8, 12, 16}, {24, 24, 8, 8}, {6, 4, 8, 10},  {8, 2, 2, 2}};
     for (const auto &s : shapes) {
         const Geom g = geom(s[0], s[1], s[2], s[3]);
+        fails += check_neighbours(g);
         for (unsigned b : {32u, 64u, 96u, 128u}) {
             fails += check_map(g, linear_map(b), "linear");
             ++maps;
