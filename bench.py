@@ -57,13 +57,12 @@ def fp64_nominal_tflops(sm_count: int, sm_mhz: float) -> float:
 
 
 # DRAM bytes (read + write) per launch of Q_tm's launch B from ncu captures of
-# the dominant kernel (FP64 and double-float on 24^3x48, FP32/FP16 on
-# 32^3x64), scaled to a full launch by the site count, valid only for the
-# kernel sources they were taken from (hash of csrc/tm_device.cuh +
+# the dominant kernel on the 32^3x64 workload lattice (per site, so that
+# another lattice scales by its site count), valid only for the kernel
+# sources they were taken from (hash of csrc/tm_device.cuh +
 # csrc/tm_kernels.cu).
-TRAFFIC = {"src": "c21978e1c0ace148",
-           "per_site": {("f64", 18): (512742400 + 35243264) / 331776, ("f64x", 18): (513207552 + 34457088) / 331776,
-                        ("f32", 12): (607362048 + 69624320) / 1048576, ("f16", 12): (312105984 + 28393984) / 1048576}}
+TRAFFIC = {"src": "3be4444c6e1f0cb8",
+           "per_site": {("f64", 18): 1791248128 / 1048576, ("f64x", 18): 1790081792 / 1048576, ("f32", 12): 689401344 / 1048576, ("f16", 12): 338128128 / 1048576}}
 
 
 def kernel_source_hash() -> str:
