@@ -59,6 +59,9 @@ def _bind(lib):
     lib.oracle_Qtm_dagger.argtypes = [I4, I4, P, D, D, P, P]
     lib.oracle_Qnd.argtypes = [I4, I4, P, D, D, D, P, P, P, P]
     lib.oracle_Qnd.restype = ctypes.c_int
+    lib.oracle_clover_site.argtypes = [I4, P, D, D, L, P]
+    lib.oracle_Qsw.argtypes = [I4, I4, P, D, D, D, P, P]
+    lib.oracle_Qsw.restype = ctypes.c_int
     lib.oracle_cg_QdagQ.argtypes = [I4, I4, P, D, D, P, P, D, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(D)]
     lib.oracle_cg_QdagQ.restype = ctypes.c_int
@@ -171,6 +174,23 @@ def Qnd(dims, U, psi_s, psi_c, kappa, mu_sigma, mu_delta, bc=ANTIPERIODIC_T):
     if not ok:
         raise ValueError("Qnd: the site-local matrix M_oo is singular")
     return out_s, out_c
+
+
+def clover_site(dims, U, csw, kappa, lex):
+    """The clover term T(x) = csw kappa i sum_{mu<nu} sigma_munu F_munu(x) at site lex, 12x12 (spin*3+colour)."""
+    U = _c(U)
+    T = np.empty((12, 12), dtype=np.complex128)
+    _load().oracle_clover_site(_i4(dims), _p(U), float(csw), float(kappa), int(lex), _p(T))
+    return T
+
+
+def Qsw(dims, U, psi_e, kappa, mu, csw, bc=ANTIPERIODIC_T):
+    """The clover twisted-mass operator Q_sw on an even-site field.  Raises ValueError if A_oo is singular."""
+    U, psi_e = _c(U), _c(psi_e)
+    out = np.empty_like(psi_e)
+    if not _load().oracle_Qsw(_i4(dims), _i4(bc), _p(U), float(kappa), float(mu), float(csw), _p(psi_e), _p(out)):
+        raise ValueError("Qsw: a site matrix A_oo is singular")
+    return out
 
 
 def cg_QdagQ(dims, U, b_e, kappa, mu, tol=1e-10, maxiter=10000, x0=None, bc=ANTIPERIODIC_T):

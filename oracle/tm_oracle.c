@@ -39,7 +39,9 @@
  * hermiticity; the literal adjoint against the dense conjugate transpose;
  * CG against a dense solve; the force against finite differences of the
  * action; the non-degenerate doublet against its dense Schur complement and
- * its flavour-diagonal (mu_delta = 0) limit.
+ * its flavour-diagonal (mu_delta = 0) limit; the clover operator against
+ * its dense Schur complement with an independently computed field strength,
+ * its c_sw = 0 limit, gauge covariance and Q_sw(mu)^dag = Q_sw(-mu).
  */
 #include <complex.h>
 #include <math.h>
@@ -530,6 +532,196 @@ int oracle_Qnd(const int dims[4], const int bc[4], const double complex *U, doub
         free(w[f]);
     }
     return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Clover (Sheikholeslami-Wohlert) twisted-mass operator                */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The clover-improved twisted-mass operator of the tmLQCD suite (the
+ * paper's introduction lists it among the suite's operators), in the
+ * hopping-parameter normalisation:
+ *
+ *   M_sw  = 1 - kappa Dhop + T + i mut gamma5,
+ *   T(x)  = c_sw kappa (i/2) sum_{mu,nu} sigma_munu F_munu(x)
+ *         = c_sw kappa i sum_{mu<nu} sigma_munu F_munu(x),
+ *   sigma_munu = (i/2) [gamma_mu, gamma_nu],
+ *   F_munu(x) = (Q_munu(x) - Q_munu(x)^dag) / 8,
+ *   Q_munu(x) = the four plaquettes in the (mu, nu) plane that start and
+ *               end at x, each oriented mu before nu (the clover leaf),
+ *
+ * and Q_sw = gamma5 (A_ee - kappa^2 H_eo A_oo^-1 H_oe) with the site-local
+ * A = 1 + T + i mut gamma5 on each parity.  The links enter F periodically
+ * (the boundary sign belongs to the fermion hops only).  A_oo^-1 is the
+ * numerical inverse of each odd site's 12x12 matrix (Gauss-Jordan).
+ */
+
+/* C = op(A) op(B) for 3x3 colour matrices, op = dagger if the flag is set. */
+static void m3mul(const cplx *A, int da, const cplx *B, int db, cplx *C)
+{
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            cplx acc = 0;
+            for (int k = 0; k < 3; ++k) {
+                cplx x = da ? conj(A[k * 3 + a]) : A[a * 3 + k];
+                cplx y = db ? conj(B[b * 3 + k]) : B[k * 3 + b];
+                acc += x * y;
+            }
+            C[a * 3 + b] = acc;
+        }
+}
+
+/* link U_mu(x) */
+static const cplx *link_at(const cplx *U, long V, int mu, long x) { return U + ((long)mu * V + x) * 9; }
+
+/* one plaquette product W = A^a B^b C^c D^d (each flag: dagger) */
+static void prod4(const cplx *A, int da, const cplx *B, int db, const cplx *C, int dc, const cplx *D, int dd, cplx *W)
+{
+    cplx t1[9], t2[9];
+    m3mul(A, da, B, db, t1);
+    m3mul(t1, 0, C, dc, t2);
+    m3mul(t2, 0, D, dd, W);
+}
+
+/* Q_munu(x): the clover leaf, sum of the four plaquettes around x. */
+static void clover_leaf(const int dims[4], const cplx *U, long x, int mu, int nu, cplx Q[9])
+{
+    long V = volume(dims);
+    int w;
+    long xpm = neighbour(dims, x, mu, +1, &w), xmm = neighbour(dims, x, mu, -1, &w);
+    long xpn = neighbour(dims, x, nu, +1, &w), xmn = neighbour(dims, x, nu, -1, &w);
+    long xmm_pn = neighbour(dims, xmm, nu, +1, &w), xmm_mn = neighbour(dims, xmm, nu, -1, &w);
+    long xmn_pm = neighbour(dims, xmn, mu, +1, &w);
+    cplx P[9];
+    for (int k = 0; k < 9; ++k) Q[k] = 0;
+    /* U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag */
+    prod4(link_at(U, V, mu, x), 0, link_at(U, V, nu, xpm), 0, link_at(U, V, mu, xpn), 1, link_at(U, V, nu, x), 1, P);
+    for (int k = 0; k < 9; ++k) Q[k] += P[k];
+    /* U_nu(x) U_mu(x+nu-mu)^dag U_nu(x-mu)^dag U_mu(x-mu) */
+    prod4(link_at(U, V, nu, x), 0, link_at(U, V, mu, xmm_pn), 1, link_at(U, V, nu, xmm), 1, link_at(U, V, mu, xmm), 0, P);
+    for (int k = 0; k < 9; ++k) Q[k] += P[k];
+    /* U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu) */
+    prod4(link_at(U, V, mu, xmm), 1, link_at(U, V, nu, xmm_mn), 1, link_at(U, V, mu, xmm_mn), 0, link_at(U, V, nu, xmn), 0, P);
+    for (int k = 0; k < 9; ++k) Q[k] += P[k];
+    /* U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag */
+    prod4(link_at(U, V, nu, xmn), 1, link_at(U, V, mu, xmn), 0, link_at(U, V, nu, xmn_pm), 0, link_at(U, V, mu, x), 1, P);
+    for (int k = 0; k < 9; ++k) Q[k] += P[k];
+}
+
+/* T(x) = csw kappa i sum_{mu<nu} sigma_munu x F_munu(x) as a 12x12 matrix, index spin*3 + colour. */
+void oracle_clover_site(const int dims[4], const double complex *U, double csw, double kappa, long x,
+                        double complex *T)
+{
+    ensure_gammas();
+    for (int k = 0; k < 144; ++k) T[k] = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nu = mu + 1; nu < 4; ++nu) {
+            cplx Q[9], F[9], sig[4][4];
+            clover_leaf(dims, U, x, mu, nu, Q);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) F[a * 3 + b] = (Q[a * 3 + b] - conj(Q[b * 3 + a])) / 8.0;
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) {
+                    cplx c = 0;
+                    for (int k = 0; k < 4; ++k) c += G[mu][a][k] * G[nu][k][b] - G[nu][a][k] * G[mu][k][b];
+                    sig[a][b] = 0.5 * I * c;
+                }
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b)
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) T[(a * 3 + i) * 12 + b * 3 + j] += csw * kappa * I * sig[a][b] * F[i * 3 + j];
+        }
+}
+
+/* B = A^-1 for an n x n matrix (n <= 12), Gauss-Jordan with partial pivoting; 0 if singular. */
+static int invert_n(int n, const cplx *A, cplx *B)
+{
+    cplx M[12][24];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c) M[r][c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (cabs(M[r][c]) > cabs(M[piv][c])) piv = r;
+        if (cabs(M[piv][c]) < 1e-300) return 0;
+        for (int k = 0; k < 2 * n; ++k) {
+            cplx t = M[c][k];
+            M[c][k] = M[piv][k];
+            M[piv][k] = t;
+        }
+        cplx d = M[c][c];
+        for (int k = 0; k < 2 * n; ++k) M[c][k] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            cplx f = M[r][c];
+            for (int k = 0; k < 2 * n; ++k) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) B[r * n + c] = M[r][c + n];
+    return 1;
+}
+
+/* A(x) = 1 + T(x) + i mut gamma5 at every site of parity p, or its inverse (inv);
+ * out[i] is the 12x12 matrix of the site with even-odd index i.  Returns 0 if singular. */
+static int sw_site_matrices(const int dims[4], const cplx *U, double kappa, double mu, double csw, int p, int inv,
+                            cplx *out)
+{
+    ensure_gammas();
+    long V = volume(dims);
+    double mut = 2.0 * kappa * mu;
+    cplx T[144], A[144];
+    for (long x = 0; x < V; ++x) {
+        int c[4];
+        coords(dims, x, c);
+        if (parity_of(c) != p) continue;
+        oracle_clover_site(dims, U, csw, kappa, x, T);
+        for (int r = 0; r < 12; ++r)
+            for (int q = 0; q < 12; ++q)
+                A[r * 12 + q] = T[r * 12 + q] + (r == q ? 1.0 : 0.0) +
+                                ((r % 3) == (q % 3) ? I * mut * G[4][r / 3][q / 3] : 0.0);
+        cplx *dst = out + (x / 2) * 144;
+        if (inv) {
+            if (!invert_n(12, A, dst)) return 0;
+        } else {
+            for (int k = 0; k < 144; ++k) dst[k] = A[k];
+        }
+    }
+    return 1;
+}
+
+static void site_matvec(long n, const cplx *M, const cplx *in, cplx *out)
+{
+    for (long i = 0; i < n; ++i)
+        for (int r = 0; r < 12; ++r) {
+            cplx acc = 0;
+            for (int q = 0; q < 12; ++q) acc += M[i * 144 + r * 12 + q] * in[i * SPINOR + q];
+            out[i * SPINOR + r] = acc;
+        }
+}
+
+/* out_e = Q_sw in_e = gamma5 (A_ee - kappa^2 H_eo A_oo^-1 H_oe) in_e; returns 0 if A_oo is singular. */
+int oracle_Qsw(const int dims[4], const int bc[4], const double complex *U, double kappa, double mu, double csw,
+               const double complex *in_e, double complex *out_e)
+{
+    long Vh = volume(dims) / 2, n = Vh * SPINOR;
+    cplx *Ae = malloc(sizeof(cplx) * Vh * 144), *Aoi = malloc(sizeof(cplx) * Vh * 144);
+    cplx *t = malloc(sizeof(cplx) * n), *u = malloc(sizeof(cplx) * n), *v = malloc(sizeof(cplx) * n),
+         *w = malloc(sizeof(cplx) * n);
+    int ok = sw_site_matrices(dims, U, kappa, mu, csw, 0, 0, Ae) && sw_site_matrices(dims, U, kappa, mu, csw, 1, 1, Aoi);
+    if (ok) {
+        oracle_hopping(dims, bc, U, 1, in_e, t, 0);              /* H_oe in */
+        for (long k = 0; k < n; ++k) t[k] *= -kappa;              /* M_oe in */
+        site_matvec(Vh, Aoi, t, u);                               /* A_oo^-1 M_oe in */
+        oracle_hopping(dims, bc, U, 0, u, v, 0);                  /* H_eo ... */
+        for (long k = 0; k < n; ++k) v[k] *= -kappa;              /* M_eo A_oo^-1 M_oe in */
+        site_matvec(Vh, Ae, in_e, w);                             /* A_ee in */
+        for (long k = 0; k < n; ++k) w[k] -= v[k];
+        oracle_gamma5(Vh, w, out_e);
+    }
+    free(Ae); free(Aoi); free(t); free(u); free(v); free(w);
+    return ok;
 }
 
 /* ------------------------------------------------------------------ */

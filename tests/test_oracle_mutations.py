@@ -2,7 +2,8 @@
 of the oracle's C source (a flipped projector sign, U where U^dag belongs,
 the backward link taken at the wrong site, the boundary sign dropped, the
 sign of M_oo^-1 or of kappa flipped, one force term with the wrong sign,
-the doublet's flavour splitting or twist or M_oo^-1 wrong),
+the doublet's flavour splitting or twist or M_oo^-1 wrong, the clover
+field strength's normalisation, a leaf's orientation or sigma's factor i),
 builds it into a scratch library, points the oracle at it and requires at
 least one of the oracle pins to fail.  The unmodified oracle passes the same
 pins.  CPU only; the planted mistakes live in temporary files only."""
@@ -16,6 +17,7 @@ import oracle as O
 
 import test_oracle_nd_pins as nd_pins
 import test_oracle_pins as pins
+import test_oracle_sw_pins as sw_pins
 
 SRC = os.path.join(os.path.dirname(O.__file__), "tm_oracle.c")
 
@@ -35,6 +37,11 @@ MUTANTS = [
     ("doublet: twist without tau3", "I * mubar * G[4][a][b] * tau3[f][g]", "I * mubar * G[4][a][b] * (f == g ? 1.0 : 0.0)"),
     ("doublet: M_oo instead of M_oo^-1", "nd_apply(Vh, Ainv, t[0], t[1], u[0], u[1]);",
      "nd_apply(Vh, A, t[0], t[1], u[0], u[1]);"),
+    ("clover: field strength normalisation", "(Q[a * 3 + b] - conj(Q[b * 3 + a])) / 8.0",
+     "(Q[a * 3 + b] - conj(Q[b * 3 + a])) / 4.0"),
+    ("clover: one leaf with a link not daggered", "link_at(U, V, mu, xpn), 1, link_at(U, V, nu, x), 1, P);",
+     "link_at(U, V, mu, xpn), 0, link_at(U, V, nu, x), 1, P);"),
+    ("clover: sigma without its factor i", "sig[a][b] = 0.5 * I * c;", "sig[a][b] = 0.5 * c;"),
 ]
 
 
@@ -53,6 +60,9 @@ def run_pins():
         (nd_pins.test_Qnd_matches_dense_schur_complement, ((2, 2, 2, 2),)),
         (nd_pins.test_Qnd_without_splitting_is_two_degenerate_operators, ()),
         (nd_pins.test_Qnd_adjoint_is_Qnd_with_minus_mu_sigma, ()),
+        (sw_pins.test_clover_term_matches_path_walk, ((2, 2, 2, 2),)),
+        (sw_pins.test_Qsw_matches_dense_schur_complement, ((2, 2, 2, 2),)),
+        (sw_pins.test_Qsw_adjoint_is_Qsw_with_minus_mu, ()),
     ]
     failed = []
     for fn, args in cases:
