@@ -409,9 +409,10 @@ def gpu_arm(args) -> None:
             del sp, dp
 
     # ---- the non-degenerate twisted doublet (two flavours, links loaded once for both)
-    nd = None
+    nd = sw = None
     if not args.no_table:
         nd = nd_section(args, ctx, tmhop, torch, F, U, DIMS, vh, hbm_peak, allmax)
+        sw = clover_section(args, ctx, tmhop, torch, F, U, DIMS, vh, hbm_peak, allmax)
 
     # ---- CG on Q^dag Q to true relative residual 1e-10: FP64 vs mixed precision
     cg = None
@@ -475,7 +476,7 @@ def gpu_arm(args) -> None:
                               f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"),
             "gflops": round(gflops, 2), "roofline": roofline, "fp64_probe": probe, "hbm_peak_gbs": hbm_peak,
             "hbm_peak_source": hbm_src,
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "nd_doublet": nd, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "nd_doublet": nd, "clover": sw, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -525,6 +526,56 @@ def nd_section(args, ctx, tmhop, torch, F, U, dims, vh, hbm_peak, allmax) -> dic
         del ins, outs
     out["note"] = ("bytes per even site: launch A 2 x (in + out) + 8 links, launch B 2 x (in + out + x) + 8 links; "
                    "flops counted: the two flavours' hops (2 x 2 x 1320)")
+    return out
+
+
+def clover_section(args, ctx, tmhop, torch, F, U, dims, vh, hbm_peak, allmax) -> dict:
+    """The clover twisted-mass operator Q_sw (c_sw = 1.76) on the workload
+    lattice in FP64-18 and FP32-12: ms per application and launch B's
+    algorithmic GB/s (per even site: the input, the output, 8 links and the
+    site's two 6x6 complex blocks, plus the re-read input in launch B), and
+    the one-time cost of building the blocks."""
+    psi = F.gaussian_spinor(vh, F.SEED_PROD_32, 1)
+    out = {"csw": 1.76}
+    stream = torch.cuda.current_stream()
+    for prec, recon in (("f64", 18), ("f32", 12)):
+        g = ctx.gauge(dims, U, prec, recon)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        C = ctx.clover(g, U, 1.76, KAPPA, MU)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        setup_ms = e0.elapsed_time(e1)
+        src, dst = ctx.pack(psi, prec), ctx.empty(vh, prec)
+        n = max(3, min(args.steps, args.table_steps))
+        for _ in range(args.warmup):
+            ctx.Qsw(g, C, dst, src)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+        for trio in ev:
+            for e in trio:
+                e.record(stream)
+        torch.cuda.synchronize()
+        for k in range(n):
+            tmhop.tm_ctx_trace(ctx.handle, ev[k])
+            ctx.Qsw(g, C, dst, src)
+        tmhop.tm_ctx_trace(ctx.handle, None)
+        torch.cuda.synchronize()
+        total = allmax(sum(e[0].elapsed_time(e[2]) for e in ev) / n)
+        kb = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+        sp = 24 * REAL[prec]
+        blocks = 72 * 2 * REAL[prec]
+        b_bytes = 3 * sp + 8 * recon * REAL[prec] + blocks
+        a_bytes = 2 * sp + 8 * recon * REAL[prec] + blocks
+        gbs = vh * b_bytes / (kb * 1e-3) / 1e9
+        out[f"{prec}-{recon}"] = {"ms_per_qsw": round(total, 4), "kernel_b_ms": round(kb, 4),
+                                  "GBps": round(vh * (a_bytes + b_bytes) / (total * 1e-3) / 1e9, 1),
+                                  "kernel_b_GBps": round(gbs, 1), "kernel_b_hbm_frac": round(gbs / hbm_peak, 4),
+                                  "block_setup_ms": round(setup_ms, 2),
+                                  "block_bytes": tmhop.tm_clover_bytes(C)}
+        tmhop.tm_clover_destroy(C)
+        g.close()
+        del src, dst
     return out
 
 

@@ -222,6 +222,34 @@ tm_status tm_Qtm(tm_ctx *ctx, const tm_gauge *U, void *out_e_dev, const void *in
 tm_status tm_Qnd(tm_ctx *ctx, const tm_gauge *U, void *out_s_dev, void *out_c_dev, const void *in_s_dev,
                  const void *in_c_dev, double kappa, double mu_sigma, double mu_delta, int sign, void *stream);
 
+/* The clover-improved twisted-mass operator (the Sheikholeslami-Wohlert
+ * term; the paper's introduction lists the suite's operators):
+ *   M_sw = 1 - kappa Dhop + T + i mut gamma5,  mut = 2 kappa mu,
+ *   T(x) = c_sw kappa i sum_{mu<nu} sigma_munu F_munu(x),  sigma_munu = (i/2)[gamma_mu, gamma_nu],
+ *   F_munu(x) = (Q_munu(x) - Q_munu(x)^dag) / 8, Q_munu(x) the sum of the four
+ *   plaquettes of the (mu, nu) plane that start and end at x (links periodic),
+ *   Q_sw = gamma5 (A_ee - kappa^2 H_eo A_oo^-1 H_oe) on even sites, A = 1 + T + i mut gamma5.
+ * tm_clover_create computes, from the canonical links U_dev (complex double
+ * [4][V][3][3], the same field U was made from), the two 6x6 chirality blocks
+ * of A on every site for both signs of mu: A itself on even sites and
+ * -kappa^2 A^-1 on odd sites (FP64 arithmetic, stored in U's precision;
+ * TM_F64 and TM_F32 only).  kappa, mu and c_sw are fixed at creation; a
+ * singular site matrix gives TM_ERR_ARG.  Synchronous with respect to
+ * stream.  The handle owns its device memory (tm_clover_bytes: 4 x 36
+ * complex numbers per site). */
+typedef struct tm_clover tm_clover;
+tm_status tm_clover_create(tm_ctx *ctx, const tm_gauge *U, const double *U_dev, double csw, double kappa, double mu,
+                           void *stream, tm_clover **out);
+void tm_clover_destroy(tm_clover *C);
+size_t tm_clover_bytes(const tm_clover *C);
+
+/* out_e = Q_sw(sign * mu) in_e with the kappa, mu and c_sw of C (sign = -1
+ * gives Q_sw(-mu) = Q_sw(mu)^dagger; c_sw = 0 gives tm_Qtm).  Two launches
+ * like tm_Qtm, the blocks applied in their epilogues; the odd temporary
+ * lives in ctx's scratch.  Traced like tm_Qtm. */
+tm_status tm_Qsw(tm_ctx *ctx, const tm_gauge *U, const tm_clover *C, void *out_e_dev, const void *in_e_dev, int sign,
+                 void *stream);
+
 /* ---- solver ------------------------------------------------------------- */
 
 /* Parameters of tm_cg_QdagQ. */

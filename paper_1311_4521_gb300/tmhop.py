@@ -89,6 +89,10 @@ def _load() -> ctypes.CDLL:
         "tm_slab_face_bytes": ([P], S),
         "tm_ctx_set_tune_cache": ([P, ctypes.c_char_p], I),
         "tm_Qnd": ([P, P, P, P, P, P, D, D, D, I, P], I),
+        "tm_clover_create": ([P, P, P, D, D, D, P, ctypes.POINTER(P)], I),
+        "tm_clover_destroy": ([P], None),
+        "tm_clover_bytes": ([P], S),
+        "tm_Qsw": ([P, P, P, P, P, I, P], I),
         "tm_ctx_set_batch_config": ([P, I, ctypes.c_uint], I),
         "tm_gauge_tune": ([P, P, P], I),
         "tm_gauge_set_map": ([P, P, ctypes.c_char_p], I),
@@ -303,6 +307,25 @@ def tm_Qnd(ctx, U, out_s, out_c, in_s, in_c, kappa, mu_sigma, mu_delta, sign=1, 
                            float(mu_delta), int(sign), _stream(stream)))
 
 
+def tm_clover_create(ctx, U, U_dev, csw, kappa, mu, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(ctx, lib.tm_clover_create(ctx, U, _ptr(U_dev), float(csw), float(kappa), float(mu), _stream(stream),
+                                     ctypes.byref(h)))
+    return h
+
+
+def tm_clover_destroy(C) -> None:
+    lib.tm_clover_destroy(C)
+
+
+def tm_clover_bytes(C) -> int:
+    return int(lib.tm_clover_bytes(C))
+
+
+def tm_Qsw(ctx, U, C, out_e_dev, in_e_dev, sign=1, stream=None):
+    _check(ctx, lib.tm_Qsw(ctx, U, C, _ptr(out_e_dev), _ptr(in_e_dev), int(sign), _stream(stream)))
+
+
 def tm_ctx_set_tune_cache(ctx, path) -> None:
     """Autotune cache file of the context (None: no file)."""
     _check(ctx, lib.tm_ctx_set_tune_cache(ctx, None if path is None else str(path).encode()))
@@ -460,6 +483,14 @@ class Context:
         """(out_s, out_c) = Q_nd (in_s, in_c) on packed even fields."""
         tm_Qnd(self.handle, U.handle, outs[0], outs[1], ins[0], ins[1], kappa, mu_sigma, mu_delta, sign)
         return outs
+
+    def clover(self, U: Gauge, U_field, csw, kappa, mu) -> ctypes.c_void_p:
+        """Clover blocks for gauge handle U (U_field: the same links, complex128 (4, V, 3, 3))."""
+        return tm_clover_create(self.handle, U.handle, _as_real_dev(U_field, self.device), csw, kappa, mu)
+
+    def Qsw(self, U: Gauge, C, out, inp, sign=1):
+        tm_Qsw(self.handle, U.handle, C, out, inp, sign)
+        return out
 
     def Qtm_host(self, U: Gauge, outs, ins, kappa, mu, sign=1):
         """Q_tm on host tensors (complex128 [Vh, 4, 3], contiguous, on the CPU; pin them for overlap)."""
