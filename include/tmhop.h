@@ -328,6 +328,23 @@ enum { TM_FORCE_SU3 = 0,    /* F in su(3): U -> exp(eps T) U changes S by eps <T
 tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, const void *X_e_dev, double kappa, double mu,
                    int mode, void *stream);
 
+/* Link gradients of the linear operators, for backpropagation through them:
+ * G_dev (complex double [4][V][3][3], the canonical gauge layout) receives
+ * the gradient with respect to the complex link entries (dL = Re tr(G^dag dU)
+ * summed over links, the convention of tm_force's TM_FORCE_GRAD) of
+ *   TM_GRAD_QTM     Re <Y, Q_tm(sign*mu) X>    X, Y even fields
+ *   TM_GRAD_HOP_EO  Re <Y, H_eo X>             X odd, Y even
+ *   TM_GRAD_HOP_OE  Re <Y, H_oe X>             X even, Y odd
+ * (<a, b> = sum conj(a) b), fields packed in U's precision.  With Y the
+ * upstream gradient of an operator's output and X its input this is the
+ * operator's vector-Jacobian product with respect to U.  Computed by the
+ * force kernels (one thread per link, no atomics) after at most two hop
+ * launches; the temporaries live in ctx's workspace.  kappa and mu are
+ * used by TM_GRAD_QTM only. */
+enum { TM_GRAD_QTM = 0, TM_GRAD_HOP_EO = 1, TM_GRAD_HOP_OE = 2 };
+tm_status tm_link_grad(tm_ctx *ctx, const tm_gauge *U, double *G_dev, const void *X_dev, const void *Y_dev, int op,
+                       double kappa, double mu, int sign, void *stream);
+
 /* ---- host-resident fields --------------------------------------------------- */
 
 /* Q_tm (sign as in tm_Qtm) on n one-parity fields in host memory:

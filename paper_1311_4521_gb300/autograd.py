@@ -5,7 +5,7 @@ Spinor tensors are complex128 of shape (V/2, 4, 3) (one parity, index
 lex/2) and gauge tensors complex128 of shape (4, V, 3, 3) on the CUDA
 device.  Every computation runs in the library's kernels: forward through
 tm_hopping_eo / tm_Qtm / tm_cg_QdagQ, backward through the adjoint
-operators (the daggered hop, Q(-mu) = Q^dag) and tm_force.
+operators (the daggered hop, Q(-mu) = Q^dag), tm_link_grad and tm_force.
 
 Gradients follow PyTorch's convention for a real loss of complex inputs,
 grad = dL/dRe z + i dL/dIm z: for S, dS/dphi = 2 X with X = (Q^dag Q)^-1 phi,
@@ -14,9 +14,10 @@ value, the scaling of the spinor gradient and of the link gradient by the
 upstream gradient are library calls too (tm_spinor_dot, tm_scale_complex):
 this module only moves buffers between torch and the library.
 
-HoppingEO and Qtm are differentiable in the spinor only; asking for their
-gradient with respect to the links raises NotImplementedError (the link
-gradient is provided for the action S, through tm_force).
+HoppingEO and Qtm are differentiable in the spinor and in the links: the
+link gradient of an operator output with upstream gradient g is the
+gradient of Re <g, Op(U) psi>, computed by tm_link_grad with the force
+kernels.
 """
 from __future__ import annotations
 
@@ -68,28 +69,31 @@ class HoppingEO(torch.autograd.Function):
         out = ctx.empty(vh, prec)
         ctx.hopping_eo(g, out, pk.pack(psi), direction)
         res = pk.unpack(out, vh)
-        fctx.save_for_backward(U)
+        fctx.save_for_backward(U, psi)
         fctx.cfg = (dims, direction, prec, bc)
         g.close()
         return res
 
     @staticmethod
     def backward(fctx, grad):
-        if fctx.needs_input_grad[1]:
-            raise NotImplementedError("HoppingEO: the gradient with respect to the links is not provided "
-                                      "(the link gradient exists for the action S, see Action)")
-        (U,) = fctx.saved_tensors
+        U, psi = fctx.saved_tensors
         dims, direction, prec, bc = fctx.cfg
         ctx = context(grad.device.index)
         pk = _Packed(ctx, prec)
         g = _gauge(ctx, dims, U, prec, bc)
         vh = grad.shape[0]
-        out = ctx.empty(vh, prec)
-        # (H_eo)^dag maps even -> odd: the daggered hop with odd output, and vice versa
-        ctx.hopping_eo(g, out, pk.pack(grad.contiguous()), 1 - direction, dagger=True)
-        res = pk.unpack(out, vh)
+        gp = pk.pack(grad.contiguous())
+        res = grad_U = None
+        if fctx.needs_input_grad[0]:
+            out = ctx.empty(vh, prec)
+            # (H_eo)^dag maps even -> odd: the daggered hop with odd output, and vice versa
+            ctx.hopping_eo(g, out, gp, 1 - direction, dagger=True)
+            res = pk.unpack(out, vh)
+        if fctx.needs_input_grad[1]:
+            op = tmhop.TM_GRAD_HOP_EO if direction == tmhop.TM_EO else tmhop.TM_GRAD_HOP_OE
+            grad_U = ctx.link_grad(g, pk.pack(psi), gp, op)
         g.close()
-        return res, None, None, None, None, None
+        return res, grad_U, None, None, None, None
 
 
 class Qtm(torch.autograd.Function):
@@ -104,27 +108,29 @@ class Qtm(torch.autograd.Function):
         out = ctx.empty(vh, prec)
         ctx.Qtm(g, out, pk.pack(psi), kappa, mu, 1)
         res = pk.unpack(out, vh)
-        fctx.save_for_backward(U)
+        fctx.save_for_backward(U, psi)
         fctx.cfg = (dims, kappa, mu, prec, bc)
         g.close()
         return res
 
     @staticmethod
     def backward(fctx, grad):
-        if fctx.needs_input_grad[1]:
-            raise NotImplementedError("Qtm: the gradient with respect to the links is not provided "
-                                      "(the link gradient exists for the action S, see Action)")
-        (U,) = fctx.saved_tensors
+        U, psi = fctx.saved_tensors
         dims, kappa, mu, prec, bc = fctx.cfg
         ctx = context(grad.device.index)
         pk = _Packed(ctx, prec)
         g = _gauge(ctx, dims, U, prec, bc)
         vh = grad.shape[0]
-        out = ctx.empty(vh, prec)
-        ctx.Qtm(g, out, pk.pack(grad.contiguous()), kappa, mu, -1)
-        res = pk.unpack(out, vh)
+        gp = pk.pack(grad.contiguous())
+        res = grad_U = None
+        if fctx.needs_input_grad[0]:
+            out = ctx.empty(vh, prec)
+            ctx.Qtm(g, out, gp, kappa, mu, -1)
+            res = pk.unpack(out, vh)
+        if fctx.needs_input_grad[1]:
+            grad_U = ctx.link_grad(g, pk.pack(psi), gp, tmhop.TM_GRAD_QTM, kappa, mu, 1)
         g.close()
-        return res, None, None, None, None, None, None
+        return res, grad_U, None, None, None, None, None
 
 
 class Action(torch.autograd.Function):

@@ -133,6 +133,46 @@ static cudaError_t force_push_launch(const tm_gauge *U, const void *Xe, const vo
     return cudaGetLastError();
 }
 
+// out = gamma5 in on a packed field (spins 2 and 3 negated)
+template <int P>
+__global__ void __launch_bounds__(256) k_gamma5(unsigned vh, const void *__restrict__ in, void *__restrict__ out)
+{
+    using R = typename SpinorIO<P>::R;
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= vh) return;
+    Spinor<R> s;
+    SpinorIO<P>::load(in, vh, i, s);
+    apply_g5(s);
+    SpinorIO<P>::store(out, vh, i, s);
+}
+
+static cudaError_t launch_gamma5(unsigned vh, int prec, const void *in, void *out, cudaStream_t s)
+{
+    if (vh == 0) return cudaSuccess;
+    const unsigned grid = (vh + 255) / 256;
+    if (prec == F64) k_gamma5<F64><<<grid, 256, 0, s>>>(vh, in, out);
+    else if (prec == F64X) k_gamma5<F64X><<<grid, 256, 0, s>>>(vh, in, out);
+    else if (prec == F32) k_gamma5<F32><<<grid, 256, 0, s>>>(vh, in, out);
+    else k_gamma5<F16><<<grid, 256, 0, s>>>(vh, in, out);
+    return cudaGetLastError();
+}
+
+// The owner-scheme link kernel for every storage format.
+static cudaError_t force_owner(const tm_gauge *U, const void *Xe, const void *Ye, const void *Zo, const void *Bo,
+                               double kappa2, int mode, double *F, cudaStream_t s)
+{
+    switch (U->prec * 100 + U->recon) {
+    case F64 * 100 + 18: return force_launch<F64, 18>(U, Xe, Ye, Zo, Bo, kappa2, mode, F, s);
+    case F64 * 100 + 12: return force_launch<F64, 12>(U, Xe, Ye, Zo, Bo, kappa2, mode, F, s);
+    case F32 * 100 + 18: return force_launch<F32, 18>(U, Xe, Ye, Zo, Bo, kappa2, mode, F, s);
+    case F32 * 100 + 12: return force_launch<F32, 12>(U, Xe, Ye, Zo, Bo, kappa2, mode, F, s);
+    case F16 * 100 + 12: return force_launch<F16, 12>(U, Xe, Ye, Zo, Bo, kappa2, mode, F, s);
+    case F64X * 100 + 18: return force_launch<F64X, 18>(U, Xe, Ye, Zo, Bo, kappa2, mode, F, s);
+    case F64X * 100 + 12: return force_launch<F64X, 12>(U, Xe, Ye, Zo, Bo, kappa2, mode, F, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 // gamma5 (1 + i mut gamma5) / (1 + mut^2): upper (1 + i mut) d, lower -(1 - i mut) d
 Coef coef_force_b(double mut)
 {
@@ -224,4 +264,55 @@ extern "C" tm_status tm_force(tm_ctx *ctx, const tm_gauge *U, double *F_dev, con
                               double mu, int mode, void *stream)
 {
     return tm_force_ex(ctx, U, F_dev, X_e_dev, kappa, mu, mode, TM_FORCE_OWNER, stream);
+}
+
+// The link gradient of a bilinear form: the force kernel computes, for any
+// full-lattice fields R = (Xe on even, Zo on odd) and L = (gamma5 Ye on
+// even, Bo on odd), the gradient of 2 k Re(L^dag Dhop(U) R) with respect to
+// the complex link entries (k its kappa2 argument).
+//   Q_tm:  Re <Y, Q X> = -kappa^2 Re(L^dag dDhop R) with Z = M_oo^-1 H_oe X and
+//          B = gamma5 (M_oo^-1)^dag H_oe Y (the same fields as for the force),
+//          so k = -kappa^2 / 2;
+//   H_eo:  Re <Y, H_eo X> with R = (0, X), L = (Y, 0): Ye = gamma5 Y, k = 1/2;
+//   H_oe:  Re <Y, H_oe X> with R = (X, 0), L = (0, Y): Bo = Y, k = 1/2.
+extern "C" tm_status tm_link_grad(tm_ctx *ctx, const tm_gauge *U, double *G_dev, const void *X_dev, const void *Y_dev,
+                                  int op, double kappa, double mu, int sign, void *stream)
+{
+    if (!ctx) return TM_ERR_ARG;
+    if (!U || bad_ptr(G_dev) || bad_ptr(X_dev) || bad_ptr(Y_dev))
+        return tm_fail(ctx, TM_ERR_ARG, "tm_link_grad: null or misaligned pointer");
+    if (op != TM_GRAD_QTM && op != TM_GRAD_HOP_EO && op != TM_GRAD_HOP_OE)
+        return tm_fail(ctx, TM_ERR_ARG, "tm_link_grad: op must be TM_GRAD_QTM, TM_GRAD_HOP_EO or TM_GRAD_HOP_OE");
+    if (sign != 1 && sign != -1) return tm_fail(ctx, TM_ERR_ARG, "tm_link_grad: sign must be +1 or -1");
+    const unsigned vh = U->geom.vh;
+    const size_t fb = align256(spinor_bytes(vh, U->prec));
+    void *base = nullptr;
+    tm_status st = tm_ctx_workspace(ctx, 2 * fb, &base);
+    if (st != TM_OK) return st;
+    char *w0 = static_cast<char *>(base), *w1 = w0 + fb;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *Xe, *Ye, *Zo, *Bo;
+    double k2;
+    cudaError_t e = cudaSuccess;
+    if (op == TM_GRAD_QTM) {
+        const double mut = 2.0 * kappa * mu * sign;
+        e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, X_dev, w0, nullptr, coef_qtm_a(mut), s, U->map);
+        if (e == cudaSuccess)
+            e = launch_hop(U->geom, U->prec, U->recon, false, TM_OE, U->links, Y_dev, w1, nullptr, coef_force_b(mut), s,
+                           U->map);
+        Xe = X_dev, Ye = Y_dev, Zo = w0, Bo = w1;
+        k2 = -0.5 * kappa * kappa;
+    } else if (op == TM_GRAD_HOP_EO) {
+        e = cudaMemsetAsync(w0, 0, fb, s);   // zeros for the unused halves of R and L
+        if (e == cudaSuccess) e = launch_gamma5(vh, U->prec, Y_dev, w1, s);
+        Xe = w0, Ye = w1, Zo = X_dev, Bo = w0;
+        k2 = 0.5;
+    } else {
+        e = cudaMemsetAsync(w0, 0, fb, s);
+        Xe = X_dev, Ye = w0, Zo = w0, Bo = Y_dev;
+        k2 = 0.5;
+    }
+    if (e == cudaSuccess) e = force_owner(U, Xe, Ye, Zo, Bo, k2, TM_FORCE_GRAD, G_dev, s);
+    if (e != cudaSuccess) return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_link_grad: ") + cudaGetErrorString(e));
+    return TM_OK;
 }

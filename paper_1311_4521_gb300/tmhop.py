@@ -25,6 +25,7 @@ TM_EO, TM_OE = 0, 1
 TM_FORCE_SU3, TM_FORCE_GRAD = 0, 1
 TM_FORCE_OWNER, TM_FORCE_ATOMIC, TM_FORCE_HALO = 0, 1, 2
 TM_SLAB_INTERIOR, TM_SLAB_BOUNDARY, TM_SLAB_ALL = 1, 2, 3
+TM_GRAD_QTM, TM_GRAD_HOP_EO, TM_GRAD_HOP_OE = 0, 1, 2
 TM_SLAB_HOP, TM_SLAB_QTM_A, TM_SLAB_QTM_B = 0, 1, 2
 PREC = {"f64": TM_F64, "f32": TM_F32, "f16": TM_F16, "f64x": TM_F64X}
 
@@ -89,6 +90,7 @@ def _load() -> ctypes.CDLL:
         "tm_slab_face_bytes": ([P], S),
         "tm_ctx_set_tune_cache": ([P, ctypes.c_char_p], I),
         "tm_Qnd": ([P, P, P, P, P, P, D, D, D, I, P], I),
+        "tm_link_grad": ([P, P, P, P, P, I, D, D, I, P], I),
         "tm_clover_create": ([P, P, P, D, D, D, P, ctypes.POINTER(P)], I),
         "tm_clover_destroy": ([P], None),
         "tm_clover_bytes": ([P], S),
@@ -307,6 +309,12 @@ def tm_Qnd(ctx, U, out_s, out_c, in_s, in_c, kappa, mu_sigma, mu_delta, sign=1, 
                            float(mu_delta), int(sign), _stream(stream)))
 
 
+def tm_link_grad(ctx, U, G_dev, X_dev, Y_dev, op, kappa=0.0, mu=0.0, sign=1, stream=None):
+    """G_dev <- gradient w.r.t. the complex links of Re <Y, Op X> (op: TM_GRAD_QTM / _HOP_EO / _HOP_OE)."""
+    _check(ctx, lib.tm_link_grad(ctx, U, _ptr(G_dev), _ptr(X_dev), _ptr(Y_dev), int(op), float(kappa), float(mu),
+                                 int(sign), _stream(stream)))
+
+
 def tm_clover_create(ctx, U, U_dev, csw, kappa, mu, stream=None) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     _check(ctx, lib.tm_clover_create(ctx, U, _ptr(U_dev), float(csw), float(kappa), float(mu), _stream(stream),
@@ -483,6 +491,12 @@ class Context:
         """(out_s, out_c) = Q_nd (in_s, in_c) on packed even fields."""
         tm_Qnd(self.handle, U.handle, outs[0], outs[1], ins[0], ins[1], kappa, mu_sigma, mu_delta, sign)
         return outs
+
+    def link_grad(self, U: Gauge, X, Y, op, kappa=0.0, mu=0.0, sign=1) -> torch.Tensor:
+        """Gradient w.r.t. the complex links of Re <Y, Op X> for packed X, Y; (4, V, 3, 3) complex128."""
+        G = torch.empty((4, 2 * U.vh, 3, 3, 2), dtype=torch.float64, device=self.device)
+        tm_link_grad(self.handle, U.handle, G, X, Y, op, kappa, mu, sign)
+        return torch.view_as_complex(G)
 
     def clover(self, U: Gauge, U_field, csw, kappa, mu) -> ctypes.c_void_p:
         """Clover blocks for gauge handle U (U_field: the same links, complex128 (4, V, 3, 3))."""

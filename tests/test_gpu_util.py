@@ -92,18 +92,3 @@ def test_action_value_matches_oracle(ctx):
     assert ok
     want = np.vdot(phi.reshape(-1), X.reshape(-1)).real
     assert abs(S.item() - want) <= 1e-11 * abs(want)
-
-
-def test_link_gradient_of_linear_operators_is_refused(ctx):
-    """Qtm and HoppingEO differentiate in the spinor only: a link gradient is
-    refused loudly instead of silently dropped."""
-    from paper_1311_4521_gb300 import autograd, tmhop
-    dims = (4, 4, 4, 4)
-    U = torch.from_numpy(F.gauge_field(dims, 94, "random")).cuda().requires_grad_(True)
-    psi = torch.from_numpy(F.gaussian_spinor(128, 94, 1)).cuda().requires_grad_(True)
-    out = autograd.qtm(psi, U, dims, 0.16, 0.01)
-    with pytest.raises(NotImplementedError):
-        torch.autograd.grad(out.abs().pow(2).sum(), (psi, U))
-    out = autograd.hopping_eo(psi, U, dims, tmhop.TM_EO)
-    with pytest.raises(NotImplementedError):
-        torch.autograd.grad(out.abs().pow(2).sum(), U)
