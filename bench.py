@@ -786,13 +786,32 @@ def batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U32=None) -> dict
     tmhop.tm_ctx_trace(ctx.handle, None)
     torch.cuda.synchronize()
     kb_ms = ev[1].elapsed_time(ev[2])
+    # the autotuner's choice for this batch, and the TMA-staged hop (code 100) forced, for comparison
+    tuned = next((ln.split()[1:3] for ln in tmhop.tm_ctx_tune_report(ctx.handle).splitlines()
+                  if ln.startswith("bhop/1/12/%dx12" % vh)), [])
+    tmhop.tm_ctx_set_batch_config(ctx.handle, 100, 0)
+    staged_b = []
+    for _ in range(4):
+        tmhop.tm_ctx_trace(ctx.handle, ev)
+        ctx.Qtm_batch([g32] * 12, outs, ins, KAPPA, MU)
+        tmhop.tm_ctx_trace(ctx.handle, None)
+        torch.cuda.synchronize()
+        staged_b.append(ev[1].elapsed_time(ev[2]))
+    tmhop.tm_ctx_set_batch_config(ctx.handle, -1, 0)
+    tmhop.tm_ctx_check(ctx.handle)
+    staged_ms = float(np.median(staged_b[1:]))
+    ctx.Qtm_batch([g32] * 12, outs, ins, KAPPA, MU)   # back to the tuned tables
     # bytes per even site and right-hand side: 2 hops of (spinor in + out + 8 links / 12) + psi_e re-read
     per = 2 * (96 + 96 + 384 / 12) + 96
     out["qtm_12rhs"] = {"ms_batched": round(ms_batch, 4), "ms_12_single_calls": round(ms_single, 4),
                         "speedup": round(ms_single / ms_batch, 2),
                         "GBps_algorithmic_amortised_links": round(12 * vh * per / (ms_batch * 1e-3) / 1e9, 1),
                         "kernel_b_ms": round(kb_ms, 4),
-                        "kernel_b_GBps": round(12 * vh * (96 + 96 + 384 / 12 + 96) / (kb_ms * 1e-3) / 1e9, 1)}
+                        "kernel_b_GBps": round(12 * vh * (96 + 96 + 384 / 12 + 96) / (kb_ms * 1e-3) / 1e9, 1),
+                        "tuned_config": " ".join(tuned),
+                        "tma_staged_kernel_b_ms": round(staged_ms, 4),
+                        "tma_staged_kernel_b_GBps": round(12 * vh * (96 + 96 + 384 / 12 + 96) / (staged_ms * 1e-3) / 1e9,
+                                                          1)}
     del ins, outs
 
     def solve_batch(gh, gl, bs):

@@ -100,13 +100,29 @@ tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on);
  * shared memory once and applied to 2 or 4 right-hand sides at a time.
  * code / 10 + 1 is the number of right-hand sides each thread computes (2:
  * one link load for both and twice the neighbour loads in flight; FP32 and
- * FP16 storage only).  Valid codes: 0, 1, 2, 4, 10, 12, 14; a code that a
- * storage format does not have (2, 10, 12, 14 for TM_F64 and TM_F64X, e.g.
- * the FP64 reliable updates of a mixed-precision batched solve) is ignored
- * for that format, which the autotuner then configures.  cap: at most this
- * many persistent CTAs (0: one per work item).  code = -1 returns to the
+ * FP16 storage only).  Code 100 is the staged hop of tm_Qtm_batch: boxes of
+ * 8 x 2 x 2 x 2 half-sites whose neighbour spinors (for every right-hand
+ * side) and links are copied into shared memory by TMA tensor copies, one
+ * persistent CTA per SM, for TM_F32 (12 or 18 reals) and TM_F16 (12)
+ * handles on lattices with Lx a multiple of 16 when some lattice of the
+ * batch has at least two right-hand sides; it builds, once per gauge handle,
+ * a site-complete copy of the links (the 8 links of every site: 1152 bytes
+ * per even-odd site pair for TM_F32 handles, which keeps all 18 reals,
+ * twice the handle's link bytes for TM_F16; freed with the handle).  Valid codes: 0, 1, 2, 4, 10, 12, 14, 100; a code that a
+ * storage format or call does not have (2, 10, 12, 14 for TM_F64 and
+ * TM_F64X, e.g. the FP64 reliable updates of a mixed-precision batched
+ * solve; 100 outside tm_Qtm_batch) is ignored there, and the autotuner
+ * configures that launch.  cap: at most this many persistent CTAs (0: one
+ * per work item; for code 100 one per SM).  code = -1 returns to the
  * autotuner. */
 tm_status tm_ctx_set_batch_config(tm_ctx *ctx, int code, unsigned cap);
+
+/* Synchronises the device and reports whether a kernel of this context gave
+ * up a bounded wait since the last check (the staged batched hop waits on
+ * shared-memory barriers for its tensor copies, each wait limited to about
+ * a second of SM clock): TM_ERR_CUDA with a message then, else TM_OK.  The
+ * flag is cleared by the check. */
+tm_status tm_ctx_check(tm_ctx *ctx);
 
 /* Text report of the launch configurations the context has chosen so far,
  * one line per batch shape: "<key> nrb=<pass width> cap=<CTA cap> ms3=<time

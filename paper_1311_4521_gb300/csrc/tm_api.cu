@@ -107,12 +107,26 @@ void tm_ctx_destroy(tm_ctx *ctx)
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->bq) cudaFree(ctx->bq);
     if (ctx->red) cudaFree(ctx->red);
+    if (ctx->dev_status) cudaFree(ctx->dev_status);
     if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
     if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     delete ctx;
 }
 
 const char *tm_last_error(const tm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+tm_status tm_ctx_check(tm_ctx *ctx)
+{
+    if (!ctx) return TM_ERR_ARG;
+    if (!ctx->dev_status) return TM_OK;
+    int v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v) e = cudaMemset(ctx->dev_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tm_ctx_check");
+    if (v) return fail(ctx, TM_ERR_CUDA, "tm_ctx_check: a bounded wait of the staged batched hop ran out");
+    return TM_OK;
+}
 
 tm_status tm_ctx_set_autotune(tm_ctx *ctx, int on)
 {
@@ -226,6 +240,7 @@ void tm_gauge_destroy(tm_gauge *g)
 {
     if (!g) return;
     if (g->links) cudaFree(g->links);
+    if (g->links8) cudaFree(g->links8);
     delete g;
 }
 

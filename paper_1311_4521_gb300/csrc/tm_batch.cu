@@ -30,7 +30,8 @@
 #include <string>
 #include <vector>
 
-#include "tm_batch.cuh"
+#include "tm_stage.cuh"
+#include "tm_stage_host.h"
 
 namespace twm {
 
@@ -256,10 +257,12 @@ cudaError_t bhop(int prec, int recon, const HopTable &t, const BSys *sys, int pa
     return cudaErrorInvalidValue;
 }
 
-// Candidate link-sharing modes for a storage format (static shared memory <= 48 KB).
-std::vector<int> nrb_candidates(int prec, int recon, int nrhs_max)
+// Candidate link-sharing modes for a storage format (static shared memory <= 48 KB),
+// and the staged hop where its tensor maps were built (`staged`).
+std::vector<int> nrb_candidates(int prec, int recon, int nrhs_max, bool staged = false)
 {
     std::vector<int> c{1};
+    if (staged) c.push_back(STAGE_CODE);
     if (nrhs_max <= 1) return c;
     c.push_back(0);
     if (prec != F64 && prec != F64X) c.push_back(2);
@@ -275,7 +278,7 @@ std::vector<int> nrb_candidates(int prec, int recon, int nrhs_max)
 
 // Fills a hop table for pass width nrb and uploads it to `dev` (capacity ngroups).
 cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_cap, HopTable &t, BGroup *dev,
-                        cudaStream_t st, std::vector<BGroup> &host)
+                        cudaStream_t st, std::vector<BGroup> &host, const StageArgs &sa = StageArgs{})
 {
     host = tmpl;
     const int w = code_nrb(nrb), rpt = code_rpt(nrb);
@@ -283,9 +286,16 @@ cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_
     unsigned item = 0;
     for (auto &g : host) {
         g.item0 = item;
+        if (nrb == STAGE_CODE) {   // boxes of STS sites, all right-hand sides of a box in one item
+            g.ntiles = g.g.vh / STS;
+            g.sbz = stage_zblock(g.g);
+            item += g.ntiles;
+            continue;
+        }
         g.ntiles = cdiv(g.g.vh, ts);
         item += w <= 1 ? g.ntiles * cdiv(unsigned(g.nrhs), unsigned(rpt)) : g.ntiles;
     }
+    t.sa = sa;
     t.nrb = nrb;
     t.nitems = item;
     t.grid = std::max(1u, std::min(item, grid_cap));
@@ -324,8 +334,11 @@ float time_table(int prec, int recon, const HopTable &t, const BSys *sys, int ri
 // Picks the pass width and persistent grid of a batched hop by timing, with a
 // per-context cache keyed by precision and the shape of the batch.
 cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<BGroup> &tmpl, BGroup *dev,
-                           const BSys *sys, int rin, int rout, HopTable &out, cudaStream_t st)
+                           const BSys *sys, int rin, int rout, HopTable &out, cudaStream_t st,
+                           const StageArgs *sa = nullptr)
 {
+    const StageArgs no_stage{};
+    const StageArgs &sta = sa ? *sa : no_stage;
     int nrhs_max = 0;
     std::string key = "bhop/" + std::to_string(prec) + "/" + std::to_string(recon);
     for (auto &g : tmpl) {
@@ -335,17 +348,19 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     const unsigned sms = unsigned(std::max(1, ctx->sm_count));
     std::vector<BGroup> host;
     if (ctx->batch_code >= 0) {   // a configuration set by the caller, where this format has it
-        const std::vector<int> ok = nrb_candidates(prec, recon, std::max(nrhs_max, 2));
+        const std::vector<int> ok = nrb_candidates(prec, recon, std::max(nrhs_max, 2), sa != nullptr);
         if (std::find(ok.begin(), ok.end(), ctx->batch_code) != ok.end()) {
-            cudaError_t e = build_table(tmpl, ctx->batch_code, ctx->batch_cap ? ctx->batch_cap : 1u << 30, out, dev,
-                                        st, host);
+            const unsigned dcap = ctx->batch_code == STAGE_CODE ? sms : 1u << 30;
+            cudaError_t e = build_table(tmpl, ctx->batch_code, ctx->batch_cap ? ctx->batch_cap : dcap, out, dev,
+                                        st, host, sta);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             return e;
         }
     }
+    if (sa) key += "/staged";
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        cudaError_t e = build_table(tmpl, it->second.first, it->second.second, out, dev, st, host);
+        cudaError_t e = build_table(tmpl, it->second.first, it->second.second, out, dev, st, host, sta);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         return e;
     }
@@ -353,17 +368,18 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     int best_nrb = 1;
     unsigned best_cap = 1u << 30;
     const unsigned caps[] = {sms * 4, sms * 8, sms * 16, 1u << 30};
-    for (int nrb : nrb_candidates(prec, recon, nrhs_max)) {
+    for (int nrb : nrb_candidates(prec, recon, nrhs_max, sa != nullptr)) {
         for (unsigned cap : caps) {
+            if (nrb == STAGE_CODE && cap != caps[0]) break;   // one CTA per SM, persistent
             HopTable t;
-            cudaError_t e = build_table(tmpl, nrb, cap, t, dev, st, host);
+            cudaError_t e = build_table(tmpl, nrb, nrb == STAGE_CODE ? sms : cap, t, dev, st, host, sta);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return e;
             float ms = ctx->autotune ? time_table(prec, recon, t, sys, rin, rout, st) : 0.f;
             if (ms < best) {
                 best = ms;
                 best_nrb = nrb;
-                best_cap = cap;
+                best_cap = nrb == STAGE_CODE ? sms : cap;
             }
             if (!ctx->autotune) break;
         }
@@ -374,7 +390,7 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     }
     ctx->tuned[key] = {best_nrb, best_cap};
     ctx->tuned_ms[key] = best;
-    cudaError_t e = build_table(tmpl, best_nrb, best_cap, out, dev, st, host);
+    cudaError_t e = build_table(tmpl, best_nrb, best_cap, out, dev, st, host, sta);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
 }
@@ -416,8 +432,9 @@ tm_status group_systems(tm_ctx *ctx, int nsys, const tm_gauge *const *U, std::ve
 extern "C" tm_status tm_ctx_set_batch_config(tm_ctx *ctx, int code, unsigned cap)
 {
     if (!ctx) return TM_ERR_ARG;
-    if (code != -1 && code != 0 && code != 1 && code != 2 && code != 4 && code != 10 && code != 12 && code != 14)
-        return tm_fail(ctx, TM_ERR_ARG, "tm_ctx_set_batch_config: code must be -1, 0, 1, 2, 4, 10, 12 or 14");
+    if (code != -1 && code != 0 && code != 1 && code != 2 && code != 4 && code != 10 && code != 12 && code != 14 &&
+        code != STAGE_CODE)
+        return tm_fail(ctx, TM_ERR_ARG, "tm_ctx_set_batch_config: code must be -1, 0, 1, 2, 4, 10, 12, 14 or 100");
     ctx->batch_code = code;
     ctx->batch_cap = cap;
     return TM_OK;
@@ -447,14 +464,34 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
             if (ins.count(o)) return tm_fail(ctx, TM_ERR_ARG, "tm_Qtm_batch: an output field is also an input");
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // The staged hop is a candidate where every lattice is tiled by its boxes
+    // and some lattice has several right-hand sides (its links are shared).
+    bool staged = stage_supported(prec, recon) && stage_available();
+    size_t nrhs_max = 0;
+    for (size_t g = 0; g < handles.size(); ++g) {
+        nrhs_max = std::max(nrhs_max, members[g].size());
+        staged = staged && stage_geometry_ok(handles[g]->geom);
+    }
+    staged = staged && nrhs_max >= 2;
+    cudaError_t e = cudaSuccess;
+    if (staged) {
+        for (auto *h : handles)
+            if (e == cudaSuccess) e = stage_links8(h, s);
+        if (e == cudaSuccess && !ctx->dev_status) {
+            e = cudaMalloc(&ctx->dev_status, sizeof(int));
+            if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), s);
+        }
+        if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: staged-hop links");
+    }
     // The batch as the device tables describe it: handles (with their links
     // and sizes), fields, precision and stream.  A repeated call with the same
     // batch finds its tables and temporaries in place and only launches.
     std::vector<uintptr_t> sig{uintptr_t(prec), uintptr_t(recon), uintptr_t(nsys), uintptr_t(s),
-                               uintptr_t(ctx->batch_code + 1), uintptr_t(ctx->batch_cap)};
+                               uintptr_t(ctx->batch_code + 1), uintptr_t(ctx->batch_cap), uintptr_t(staged)};
     for (int k = 0; k < nsys; ++k) {
         sig.push_back(uintptr_t(U[k]));
         sig.push_back(uintptr_t(U[k]->links));
+        sig.push_back(uintptr_t(U[k]->links8));
         const Geom &gk = U[k]->geom;   // a handle re-created at the same address may describe another lattice
         sig.push_back((uintptr_t(gk.lx) << 48) | (uintptr_t(gk.ly) << 32) | (uintptr_t(gk.lz) << 16) | uintptr_t(gk.lt));
         sig.push_back(uintptr_t(gk.anti[0]) | uintptr_t(gk.anti[1]) << 1 | uintptr_t(gk.anti[2]) << 2 |
@@ -464,13 +501,15 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     }
     HopTable t;
     BSys *dsys = nullptr;
-    cudaError_t e = cudaSuccess;
     if (ctx->bq && sig == ctx->bq_sig) {
         t.nrb = ctx->bq_tab.nrb;
         t.grid = ctx->bq_tab.grid;
         t.nitems = ctx->bq_tab.nitems;
         t.ngroups = ctx->bq_tab.ngroups;
         t.dev = static_cast<BGroup *>(ctx->bq_tab.dgrp);
+        t.sa.smaps = static_cast<const CUtensorMap *>(ctx->bq_tab.smaps);
+        t.sa.lmaps = static_cast<const CUtensorMap *>(ctx->bq_tab.lmaps);
+        t.sa.status = ctx->dev_status;
         dsys = static_cast<BSys *>(ctx->bq_tab.dsys);
     } else {
         // the previous batch's launches may still read the buffer on another stream
@@ -483,6 +522,8 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
         size_t need = 0;
         for (int k = 0; k < nsys; ++k) need += align256(spinor_bytes(U[k]->geom.vh, prec));
         need += align256(sizeof(BSys) * nsys) + align256(sizeof(BGroup) * handles.size());
+        const size_t nsmap = size_t(nsys) * NROLE * 2 * NSH;   // [system][role][shape] field maps
+        if (staged) need += align256(sizeof(CUtensorMap) * nsmap) + align256(sizeof(CUtensorMap) * handles.size());
         if (ctx->bq_bytes < need) {
             if (ctx->bq) cudaFree(ctx->bq);
             ctx->bq = nullptr;
@@ -518,9 +559,37 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
         dsys = reinterpret_cast<BSys *>(c);
         c += align256(sizeof(BSys) * nsys);
         BGroup *dgrp = reinterpret_cast<BGroup *>(c);
+        c += align256(sizeof(BGroup) * handles.size());
         // pageable source: the copy has taken the data when the call returns
         e = cudaMemcpyAsync(dsys, hs.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = tune_hop_table(ctx, prec, recon, tmpl, dgrp, dsys, R_IN, R_T, t, s);
+        StageArgs sa{};
+        if (staged && e == cudaSuccess) {
+            // tensor maps of the two hop inputs of every system and of every group's links
+            std::vector<CUtensorMap> hm(nsmap), hl(handles.size());
+            memset(hm.data(), 0, sizeof(CUtensorMap) * nsmap);
+            bool ok = true;
+            for (int q = 0; q < nsys && ok; ++q) {
+                const Geom &gq = tmpl[size_t(std::upper_bound(tmpl.begin(), tmpl.end(), q,
+                                                              [](int v, const BGroup &G) { return v < G.sys0; }) -
+                                             tmpl.begin()) - 1].g;
+                for (int role : {int(R_IN), int(R_T)})
+                    ok = ok && stage_field_maps(prec, gq, hs[size_t(q)].f[role], &hm[(size_t(q) * NROLE + role) * 2 * NSH]);
+            }
+            for (size_t g = 0; g < handles.size() && ok; ++g) ok = stage_link_map(handles[g], hl[g]);
+            if (ok) {
+                CUtensorMap *dsm = reinterpret_cast<CUtensorMap *>(c);
+                c += align256(sizeof(CUtensorMap) * nsmap);
+                CUtensorMap *dlm = reinterpret_cast<CUtensorMap *>(c);
+                e = cudaMemcpyAsync(dsm, hm.data(), sizeof(CUtensorMap) * nsmap, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(dlm, hl.data(), sizeof(CUtensorMap) * hl.size(), cudaMemcpyHostToDevice, s);
+                sa.smaps = dsm;
+                sa.lmaps = dlm;
+                sa.status = ctx->dev_status;
+            }
+        }
+        if (e == cudaSuccess)
+            e = tune_hop_table(ctx, prec, recon, tmpl, dgrp, dsys, R_IN, R_T, t, s, sa.smaps ? &sa : nullptr);
         if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: setup");
         ctx->bq_sig = sig;
         ctx->bq_stream = s;
@@ -530,6 +599,8 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
         ctx->bq_tab.ngroups = t.ngroups;
         ctx->bq_tab.dsys = dsys;
         ctx->bq_tab.dgrp = dgrp;
+        ctx->bq_tab.smaps = t.sa.smaps;
+        ctx->bq_tab.lmaps = t.sa.lmaps;
     }
     const double mut = 2.0 * kappa * mu * sign;
     tm_trace_mark(ctx, 0, s);

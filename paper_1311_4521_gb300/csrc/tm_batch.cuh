@@ -2,6 +2,8 @@
 // the system and group tables, the batched hop kernel and its launchers.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the staged hop's tensor maps)
+
 #include "tm_cg.cuh"
 #include "tm_internal.h"
 
@@ -22,6 +24,7 @@ struct BGroup {
     int nrhs, sys0;     // systems sys0 .. sys0 + nrhs - 1
     unsigned item0;     // first work item of the group
     unsigned ntiles;    // tiles covering the group's Vh sites
+    int sbz = 1;        // staged hop: boxes per z block of its traversal order
 };
 
 constexpr int BT = 128;   // threads per CTA of the batched hop
@@ -76,6 +79,13 @@ __device__ __forceinline__ int find_group(const BGroup *gr, int ng, const unsign
 }
 
 
+// Arguments of the staged hop (tm_stage.cuh) beyond those of the batched hop.
+struct StageArgs {
+    const CUtensorMap *smaps = nullptr;  // [system][role][2 * 5]: field boxes, then FP16 norm boxes
+    const CUtensorMap *lmaps = nullptr;  // [group]: the group's site-complete links
+    int *status = nullptr;               // set to 1 when a wait of the kernel runs out
+};
+
 struct HopTable {
     int nrb = 1;            // configuration code: pass width (code % 10; <= 1: no link staging) and
                             // right-hand sides per thread (code / 10 + 1)
@@ -83,6 +93,7 @@ struct HopTable {
     unsigned nitems = 0;
     BGroup *dev = nullptr;  // device copy of the groups
     int ngroups = 0;
+    StageArgs sa{};         // tensor maps of the staged hop (configuration code 100)
 };
 
 // Launches of the batched hop for one storage format (tm_batch_hop_*.cu).

@@ -44,7 +44,9 @@ struct tm_ctx {
         int nrb = 1, ngroups = 0;
         unsigned grid = 0, nitems = 0;
         void *dsys = nullptr, *dgrp = nullptr;
+        const void *smaps = nullptr, *lmaps = nullptr;  // tensor maps of the staged hop, if built
     } bq_tab;
+    int *dev_status = nullptr;       // set by a kernel whose bounded wait ran out (tm_ctx_check)
 };
 
 // Records msg as the context's last error (tm_last_error) and returns st.
@@ -101,6 +103,7 @@ struct tm_gauge {
     size_t bytes = 0;
     twm::SiteMap map{};   // site-to-thread map of this lattice's hop launches (tm_gauge_tune)
     std::string map_name = "linear128";
+    mutable void *links8 = nullptr;  // site-complete link copy of the staged batched hop (built on first use)
 };
 
 // Gives U the site map its lattice has in the context's tune cache, if any.

@@ -91,6 +91,7 @@ def _load() -> ctypes.CDLL:
         "tm_ctx_set_tune_cache": ([P, ctypes.c_char_p], I),
         "tm_Qnd": ([P, P, P, P, P, P, D, D, D, I, P], I),
         "tm_link_grad": ([P, P, P, P, P, I, D, D, I, P], I),
+        "tm_ctx_check": ([P], I),
         "tm_clover_create": ([P, P, P, D, D, D, P, ctypes.POINTER(P)], I),
         "tm_clover_destroy": ([P], None),
         "tm_clover_bytes": ([P], S),
@@ -307,6 +308,11 @@ def tm_Qnd(ctx, U, out_s, out_c, in_s, in_c, kappa, mu_sigma, mu_delta, sign=1, 
     """The non-degenerate twisted doublet on packed even fields (see include/tmhop.h)."""
     _check(ctx, lib.tm_Qnd(ctx, U, _ptr(out_s), _ptr(out_c), _ptr(in_s), _ptr(in_c), float(kappa), float(mu_sigma),
                            float(mu_delta), int(sign), _stream(stream)))
+
+
+def tm_ctx_check(ctx):
+    """Raises TmError if a bounded device wait of the context ran out since the last check."""
+    _check(ctx, lib.tm_ctx_check(ctx))
 
 
 def tm_link_grad(ctx, U, G_dev, X_dev, Y_dev, op, kappa=0.0, mu=0.0, sign=1, stream=None):
