@@ -633,10 +633,41 @@ def only_section(args, ctx, tmhop, torch, F, U, psi, dims, vh, barrier, allmax) 
     cg         the CG section on --cg-lattice;
     force      the force call (3 hops + assembly by --force-scheme) on
                --lattice, --steps calls;
-    solve      the even-odd full-lattice solve on --lattice (FP32 inner)."""
+    solve      the even-odd full-lattice solve on --lattice (FP32 inner);
+    nd         the non-degenerate doublet Q_nd on --lattice, --steps calls;
+    clover     the clover operator Q_sw (c_sw 1.76) on --lattice, --steps calls.
+    --batch-code fixes the batched hop's configuration for batch-qtm (e.g.
+    100, the TMA-staged hop); -1 leaves it to the autotuner."""
     res = {"only": args.only, "lattice": list(dims)}
     stream = torch.cuda.current_stream()
-    if args.only == "batch-qtm":
+    def timed_calls(fn):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    if args.only == "nd":
+        g = ctx.gauge(dims, U, args.prec, args.recon)
+        ins = [ctx.pack(psi, args.prec), ctx.pack(F.gaussian_spinor(vh, F.SEED_PROD_32, 2), args.prec)]
+        outs = [ctx.empty(vh, args.prec), ctx.empty(vh, args.prec)]
+        res["ms_per_qnd"] = timed_calls(lambda: ctx.Qnd(g, outs, ins, KAPPA, 0.0015, 0.0018))
+        g.close()
+    elif args.only == "clover":
+        g = ctx.gauge(dims, U, args.prec, args.recon)
+        C = ctx.clover(g, U, 1.76, KAPPA, MU)
+        src, dst = ctx.pack(psi, args.prec), ctx.empty(vh, args.prec)
+        res["ms_per_qsw"] = timed_calls(lambda: ctx.Qsw(g, C, dst, src))
+        tmhop.tm_clover_destroy(C)
+        g.close()
+    elif args.only == "batch-qtm":
+        tmhop.tm_ctx_set_batch_config(ctx.handle, args.batch_code, 0)
+        res["batch_code"] = args.batch_code
         g = ctx.gauge(dims, U, args.prec, args.recon)
         ins = [ctx.pack(F.gaussian_spinor(vh, F.SEED_BATCH_RHS + j, 0), args.prec) for j in range(12)]
         outs = [ctx.empty(vh, args.prec) for _ in range(12)]
@@ -650,6 +681,8 @@ def only_section(args, ctx, tmhop, torch, F, U, psi, dims, vh, barrier, allmax) 
         e1.record(stream)
         torch.cuda.synchronize()
         res["ms_per_batched_qtm"] = e0.elapsed_time(e1) / args.steps
+        tmhop.tm_ctx_check(ctx.handle)
+        tmhop.tm_ctx_set_batch_config(ctx.handle, -1, 0)
         g.close()
     elif args.only == "cg":
         args.cg_lattice = dims
@@ -949,8 +982,10 @@ def main() -> None:
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
-    ap.add_argument("--only", choices=["batch-qtm", "cg", "force", "solve"], default=None,
+    ap.add_argument("--only", choices=["batch-qtm", "cg", "force", "solve", "nd", "clover"], default=None,
                     help="run one section alone (for profiling captures)")
+    ap.add_argument("--batch-code", type=int, default=-1,
+                    help="batched-hop configuration for --only batch-qtm (-1: autotuned; 100: TMA-staged)")
     ap.add_argument("--cg-delta", type=float, default=-1.0,
                     help="reliable-update threshold of the mixed-precision solvers (residual drop factor); "
                          "negative: the library's automatic choice (FP32 1e-3, FP16 0.022)")

@@ -22,11 +22,18 @@
 
 namespace twm {
 
+// Resident CTAs per SM the pair hop is compiled for.  Measured on 32^3x64
+// (Q_nd, FP32-12 / FP16-12): 3 CTAs (168 registers) 0.342 / 0.277 ms, 4 (128
+// registers, 16 bytes of spills) 0.332 / 0.255 ms, 2 0.407 / 0.277 ms.  One
+// thread per (site, flavour) instead, the flavours on adjacent lanes sharing
+// each link load and mixed by shuffles, was slower at every occupancy
+// (0.359-0.384 / 0.291-0.298 ms): the pair form's single link load and
+// reconstruction per site outweigh its lower occupancy.
 #ifndef TM_ND_MINB_F64
 #define TM_ND_MINB_F64 1
 #endif
 #ifndef TM_ND_MINB_F32
-#define TM_ND_MINB_F32 3
+#define TM_ND_MINB_F32 4
 #endif
 #define TM_ND_MINB(P) ((P) == F64 ? TM_ND_MINB_F64 : TM_ND_MINB_F32)
 
