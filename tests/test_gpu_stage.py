@@ -38,10 +38,10 @@ def _batch(spec, seed0):
     return lats, systems
 
 
-def _run(ctx, prec, recon, spec, code, cap, seed0, signs=(1, -1)):
+def _run(ctx, prec, recon, spec, code, cap, seed0, signs=(1, -1), bc=(-1, 1, 1, 1)):
     from paper_1311_4521_gb300 import tmhop
     lats, systems = _batch(spec, seed0)
-    gauges = [ctx.gauge(d, U, prec, recon) for d, U in lats]
+    gauges = [ctx.gauge(d, U, prec, recon, bc) for d, U in lats]
     ins = [ctx.pack(psi, prec) for _, psi in systems]
     try:
         tmhop.tm_ctx_set_batch_config(ctx.handle, code, cap)
@@ -54,7 +54,7 @@ def _run(ctx, prec, recon, spec, code, cap, seed0, signs=(1, -1)):
             for (li, psi), out in zip(systems, outs):
                 dims, U = lats[li]
                 got = ctx.unpack(out, psi.shape[0], prec).cpu().numpy()
-                want = O.Qtm(dims, U, psi, 0.1394, sign * 0.0015)
+                want = O.Qtm(dims, U, psi, 0.1394, sign * 0.0015, bc=bc)
                 assert np.all(np.isfinite(got)), (prec, recon, dims, sign)
                 assert rel(got, want) < TOL[prec], (prec, recon, dims, sign, rel(got, want))
     finally:
@@ -91,3 +91,12 @@ def test_staged_code_ignored_where_unavailable(ctx):
     configures the launch; the result is still right."""
     spec = [((8, 8, 8, 8), 3)]
     _run(ctx, "f32", 12, spec, 100, 0, 950, signs=(1,))
+
+
+@pytest.mark.parametrize("bc", [(1, -1, -1, 1), (-1, 1, -1, -1), (1, 1, 1, 1)])
+def test_staged_hop_boundary_signs(ctx, bc):
+    """Antiperiodic boundaries in x, y or z (bc is (t, x, y, z)): the wrap
+    signs of the staged hop come from the lattice's boundary flags, not from
+    the position in the box."""
+    spec = [((32, 4, 4, 6), 2)]
+    _run(ctx, "f32", 12, spec, 100, 2, 990, signs=(1,), bc=bc)
