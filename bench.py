@@ -820,7 +820,7 @@ def batch_section(args, ctx, tmhop, torch, F, allmax, barrier, U32=None) -> dict
     torch.cuda.synchronize()
     kb_ms = ev[1].elapsed_time(ev[2])
     # the autotuner's choice for this batch, and the TMA-staged hop (code 100) forced, for comparison
-    tuned = next((ln.split()[1:3] for ln in tmhop.tm_ctx_tune_report(ctx.handle).splitlines()
+    tuned = next(([w for w in ln.split()[1:] if not w.startswith("ms3=")] for ln in tmhop.tm_ctx_tune_report(ctx.handle).splitlines()
                   if ln.startswith("bhop/1/12/%dx12" % vh)), [])
     tmhop.tm_ctx_set_batch_config(ctx.handle, 100, 0)
     staged_b = []

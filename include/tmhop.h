@@ -126,7 +126,8 @@ tm_status tm_ctx_check(tm_ctx *ctx);
 
 /* Text report of the launch configurations the context has chosen so far,
  * one line per batch shape: "<key> nrb=<pass width> cap=<CTA cap> ms3=<time
- * of three launches at selection>", and one per lattice tuned by
+ * of three launches at selection> band=<1: tiles in z bands, t within a
+ * band; 0: lexicographic tiles>", and one per lattice tuned by
  * tm_gauge_tune: "hop/<cache key> map=<map> ms=<per launch> linear128_ms=<the
  * default map's> gain=<ratio> candidates=<n>" (or "map=<map> (cache)").  Writes at most size bytes including the
  * terminating NUL (truncating) and returns the size the full report needs;

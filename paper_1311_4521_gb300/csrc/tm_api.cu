@@ -142,8 +142,10 @@ size_t tm_ctx_tune_report(const tm_ctx *ctx, char *buf, size_t size)
     for (const auto &kv : ctx->tuned) {
         char line[256];
         auto ms = ctx->tuned_ms.find(kv.first);
-        snprintf(line, sizeof line, "%s nrb=%d cap=%u ms3=%.4f\n", kv.first.c_str(), kv.second.first,
-                 kv.second.second, ms == ctx->tuned_ms.end() ? 0.0 : double(ms->second));
+        auto band = ctx->tuned_band.find(kv.first);
+        snprintf(line, sizeof line, "%s nrb=%d cap=%u ms3=%.4f band=%d\n", kv.first.c_str(), kv.second.first,
+                 kv.second.second, ms == ctx->tuned_ms.end() ? 0.0 : double(ms->second),
+                 band == ctx->tuned_band.end() ? 1 : band->second);
         rep += line;
     }
     for (const auto &kv : ctx->tuned_maps) rep += "hop/" + kv.first + " " + kv.second + "\n";

@@ -276,9 +276,33 @@ std::vector<int> nrb_candidates(int prec, int recon, int nrhs_max, bool staged =
     return c;
 }
 
+// z planes per band of the gather hops' tile order (tile_of) on lattice g
+// with tiles of ts sites: the largest divisor of Lz whose band slab holds at
+// most TM_BATCH_BAND_SITES sites and whole tiles; 0 (lexicographic) if none.
+#ifndef TM_BATCH_BAND_SITES
+#define TM_BATCH_BAND_SITES 8192
+#endif
+int zband_for(const Geom &g, unsigned ts)
+{
+    const unsigned plane = unsigned(g.hx) * unsigned(g.ly);
+    int best = 0;
+    for (int b = 1; b < g.lz; ++b)
+        if (g.lz % b == 0 && (plane * unsigned(b)) % ts == 0 && plane * unsigned(b) <= TM_BATCH_BAND_SITES) best = b;
+    return best;
+}
+
+// Whether the gather hops of a storage format walk their tiles in z bands.
+// Measured on 32^3x64 with 12 right-hand sides (tuned configuration, Q_tm
+// per call): FP32-12 1.87 ms banded against 1.91 lexicographic (launch B
+// 0.99 against 1.02 ms: fewer neighbour re-reads from memory), FP16-12 1.743
+// against 1.721.  Timing both orders in the tuner did not separate them (its
+// launches differ by less than their spread), so the order is fixed per format.
+bool band_order(int prec) { return prec != F16; }
+
 // Fills a hop table for pass width nrb and uploads it to `dev` (capacity ngroups).
 cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_cap, HopTable &t, BGroup *dev,
-                        cudaStream_t st, std::vector<BGroup> &host, const StageArgs &sa = StageArgs{})
+                        cudaStream_t st, std::vector<BGroup> &host, const StageArgs &sa = StageArgs{},
+                        bool band = true)
 {
     host = tmpl;
     const int w = code_nrb(nrb), rpt = code_rpt(nrb);
@@ -293,6 +317,7 @@ cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_
             continue;
         }
         g.ntiles = cdiv(g.g.vh, ts);
+        g.zband = band && g.nrhs > 1 ? zband_for(g.g, ts) : 0;
         item += w <= 1 ? g.ntiles * cdiv(unsigned(g.nrhs), unsigned(rpt)) : g.ntiles;
     }
     t.sa = sa;
@@ -304,11 +329,14 @@ cudaError_t build_table(const std::vector<BGroup> &tmpl, int nrb, unsigned grid_
     return cudaMemcpyAsync(dev, host.data(), sizeof(BGroup) * host.size(), cudaMemcpyHostToDevice, st);
 }
 
-// Times a candidate hop table with a (parity 1, rin -> rout) launch; returns ms.
-// rin and rout must be fields of the table's precision.
-// Time of three hop launches with table t: the median of three rounds, so
-// that one disturbed round (clock ramp, another process's work) can neither
-// hide a slow configuration nor discard a fast one.
+// Times a candidate hop table with (parity 1, rin -> rout) launches; returns
+// ms.  rin and rout must be fields of the table's precision.  The time of
+// three launches is the median of three rounds, so that one disturbed round
+// (clock ramp, another process's work) can neither hide a slow configuration
+// nor discard a fast one.  A round is two launches without and one with the
+// second input stream of Q_tm's second hop (rout read as x before each
+// thread overwrites its own site: the traffic, not the meaning), the mix of
+// a Q_tm application.
 float time_table(int prec, int recon, const HopTable &t, const BSys *sys, int rin, int rout, cudaStream_t st)
 {
     cudaEvent_t ev[4];
@@ -318,7 +346,7 @@ float time_table(int prec, int recon, const HopTable &t, const BSys *sys, int ri
     float ms[3] = {0.f, 0.f, 0.f};
     cudaEventRecord(ev[0], st);
     for (int round = 0; round < 3; ++round) {
-        for (int r = 0; r < 3; ++r) bhop(prec, recon, t, sys, 1, rin, rout, -1, k, BH_PLAIN, 0, st);
+        for (int r = 0; r < 3; ++r) bhop(prec, recon, t, sys, 1, rin, rout, r == 2 ? rout : -1, k, BH_PLAIN, 0, st);
         cudaEventRecord(ev[round + 1], st);
     }
     cudaEventSynchronize(ev[3]);
@@ -352,7 +380,7 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
         if (std::find(ok.begin(), ok.end(), ctx->batch_code) != ok.end()) {
             const unsigned dcap = ctx->batch_code == STAGE_CODE ? sms : 1u << 30;
             cudaError_t e = build_table(tmpl, ctx->batch_code, ctx->batch_cap ? ctx->batch_cap : dcap, out, dev,
-                                        st, host, sta);
+                                        st, host, sta, band_order(prec));
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             return e;
         }
@@ -360,7 +388,8 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     if (sa) key += "/staged";
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        cudaError_t e = build_table(tmpl, it->second.first, it->second.second, out, dev, st, host, sta);
+        cudaError_t e = build_table(tmpl, it->second.first, it->second.second, out, dev, st, host, sta,
+                                    band_order(prec));
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         return e;
     }
@@ -372,7 +401,8 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
         for (unsigned cap : caps) {
             if (nrb == STAGE_CODE && cap != caps[0]) break;   // one CTA per SM, persistent
             HopTable t;
-            cudaError_t e = build_table(tmpl, nrb, nrb == STAGE_CODE ? sms : cap, t, dev, st, host, sta);
+            cudaError_t e = build_table(tmpl, nrb, nrb == STAGE_CODE ? sms : cap, t, dev, st, host, sta,
+                                        band_order(prec));
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return e;
             float ms = ctx->autotune ? time_table(prec, recon, t, sys, rin, rout, st) : 0.f;
@@ -390,7 +420,8 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     }
     ctx->tuned[key] = {best_nrb, best_cap};
     ctx->tuned_ms[key] = best;
-    cudaError_t e = build_table(tmpl, best_nrb, best_cap, out, dev, st, host, sta);
+    ctx->tuned_band[key] = band_order(prec) ? 1 : 0;
+    cudaError_t e = build_table(tmpl, best_nrb, best_cap, out, dev, st, host, sta, band_order(prec));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
 }
@@ -510,6 +541,7 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
         t.sa.smaps = static_cast<const CUtensorMap *>(ctx->bq_tab.smaps);
         t.sa.lmaps = static_cast<const CUtensorMap *>(ctx->bq_tab.lmaps);
         t.sa.status = ctx->dev_status;
+        t.sa.roles = t.sa.smaps ? (1u << R_IN) | (1u << R_T) : 0u;
         dsys = static_cast<BSys *>(ctx->bq_tab.dsys);
     } else {
         // the previous batch's launches may still read the buffer on another stream
@@ -586,6 +618,7 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
                 sa.smaps = dsm;
                 sa.lmaps = dlm;
                 sa.status = ctx->dev_status;
+                sa.roles = (1u << R_IN) | (1u << R_T);
             }
         }
         if (e == cudaSuccess)

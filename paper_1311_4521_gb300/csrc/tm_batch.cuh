@@ -25,7 +25,25 @@ struct BGroup {
     unsigned item0;     // first work item of the group
     unsigned ntiles;    // tiles covering the group's Vh sites
     int sbz = 1;        // staged hop: boxes per z block of its traversal order
+    int zband = 0;      // gather hops: z planes per band of the tile order (0: lexicographic)
 };
+
+// The tile order of the gather hops.  Lexicographic tiles reach a site's t
+// neighbours two time slices later; with 12 right-hand sides that is more
+// traffic than L2 keeps, and a third of the neighbour reads went to memory
+// again.  With bands of zband z planes the order is band, t, tile within the
+// band's slab, so the t neighbours are one band slab (a few thousand sites)
+// away; only the z neighbours across band edges are read twice.
+__device__ __forceinline__ unsigned tile_of(const BGroup &G, unsigned tno, unsigned ts)
+{
+    if (G.zband == 0) return tno;
+    const unsigned plane = unsigned(G.g.hx) * unsigned(G.g.ly);
+    const unsigned tpb = plane * unsigned(G.zband) / ts;   // tiles per band slab
+    const unsigned per_band = tpb * unsigned(G.g.lt);
+    const unsigned band = tno / per_band, rem = tno - band * per_band;
+    const unsigned t = rem / tpb, k = rem - t * tpb;
+    return (t * unsigned(G.g.lz) + band * unsigned(G.zband)) * plane / ts + k;
+}
 
 constexpr int BT = 128;   // threads per CTA of the batched hop
 // Resident CTAs per SM the batched hop is compiled for, with one and with two
@@ -84,6 +102,7 @@ struct StageArgs {
     const CUtensorMap *smaps = nullptr;  // [system][role][2 * 5]: field boxes, then FP16 norm boxes
     const CUtensorMap *lmaps = nullptr;  // [group]: the group's site-complete links
     int *status = nullptr;               // set to 1 when a wait of the kernel runs out
+    unsigned roles = 0;                  // bit r: the maps of hop-input role r are encoded
 };
 
 struct HopTable {
@@ -189,7 +208,8 @@ __global__ void __launch_bounds__(BT, RPT == 1 ? TM_BATCH_MINB : TM_BATCH_MINB_R
         const unsigned rel = item - G.item0;
         const unsigned nsets = (unsigned(G.nrhs) + RPT - 1) / RPT;   // items per tile for NRB <= 1
         const unsigned tno = NRB <= 1 ? rel / nsets : rel;
-        const unsigned i = tno * TS + tx;
+        const unsigned ptile = tile_of(G, tno, TS);   // the tile's place in the lattice
+        const unsigned i = ptile * TS + tx;
         const V *links = static_cast<const V *>(G.links);
         if (NRB > 1) {
             // skip the tile (and its link traffic) when no system of the group is active
@@ -198,7 +218,7 @@ __global__ void __launch_bounds__(BT, RPT == 1 ? TM_BATCH_MINB : TM_BATCH_MINB_R
             if (!any) continue;   // uniform over the block
             __syncthreads();  // readers of the previous tile are done
             if (ty == 0) {
-                unsigned site = tno * TS + tx;
+                unsigned site = ptile * TS + tx;
                 if (site < G.g.vh) {
                     Nbrs n;
                     neighbours(G.g, parity, site, n);
@@ -208,7 +228,7 @@ __global__ void __launch_bounds__(BT, RPT == 1 ? TM_BATCH_MINB : TM_BATCH_MINB_R
             __syncthreads();
             for (unsigned e = threadIdx.x; e < 8u * L::NCHUNK * TS; e += BT) {
                 const unsigned s = e % TS, dc = e / TS, c = dc % L::NCHUNK, d = dc / L::NCHUNK;
-                const unsigned site = tno * TS + s;
+                const unsigned site = ptile * TS + s;
                 V v{};
                 if (site < G.g.vh) {
                     const unsigned idx = d < 4 ? site : bwd_idx[(d - 4) * TS + s];

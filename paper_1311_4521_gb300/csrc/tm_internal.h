@@ -28,6 +28,7 @@ struct tm_ctx {
     unsigned batch_cap = 0;          // and its persistent CTA cap (0: one CTA per work item)
     std::map<std::string, std::pair<int, unsigned>> tuned;  // batched hop: key -> (pass width, CTA cap)
     std::map<std::string, float> tuned_ms;                  // and the winner's time for 3 launches
+    std::map<std::string, int> tuned_band;                  // and its tile order (1 banded, 0 lexicographic)
     std::map<std::string, std::string> tuned_maps;          // single-lattice hop: key -> chosen map (tm_gauge_tune)
     std::string tune_cache;          // autotune cache file ("" = none; TMHOP_TUNE_CACHE at creation)
     void *stage = nullptr;           // device staging slots of tm_Qtm_host (grow-only)

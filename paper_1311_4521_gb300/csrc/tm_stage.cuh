@@ -29,6 +29,8 @@
 // so no failure leaves the GPU waiting.
 #pragma once
 
+#include <atomic>
+
 #include "tm_batch.cuh"
 
 namespace twm {
@@ -430,13 +432,20 @@ inline cudaError_t stage_hop(const HopTable &t, const BSys *sys, int parity, int
                              int mode, int gate, cudaStream_t st)
 {
     using C = StageCfg<P, RECON>;
-    if (mode != BH_PLAIN || !t.sa.smaps || !t.sa.lmaps || !t.sa.status) return cudaErrorInvalidValue;
-    static bool attr = false;   // set once per instantiation (the attribute is per function)
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage_hop<P, RECON, BH_PLAIN>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    // only inputs whose tensor maps were encoded (a zero map must never reach a tensor copy)
+    if (mode != BH_PLAIN || !t.sa.smaps || !t.sa.lmaps || !t.sa.status || rin < 0 || rin >= NROLE ||
+        !(t.sa.roles & (1u << rin)))
+        return cudaErrorInvalidValue;
+    // the shared-memory opt-in is a per-device function attribute: set once per device
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_set.load() & bit)) {
+        e = cudaFuncSetAttribute(k_stage_hop<P, RECON, BH_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr_set.fetch_or(bit);
     }
     k_stage_hop<P, RECON, BH_PLAIN><<<t.grid, C::NT, C::SMEM, st>>>(t.dev, t.ngroups, t.nitems, sys, parity, rin,
                                                                      rout, rx, k, gate, t.sa);
