@@ -729,9 +729,10 @@ def grad_section(args, ctx, tmhop, torch, F) -> dict:
     through autograd (forward solve + backward force), and the force call
     alone (its three hops plus the force assembly) for each way of
     assembling the per-link force (one owner thread per link, pushes with
-    FP64 atomics, pushes into private buffers plus a summing pass), FP64
-    and FP32 storage (for information: correctness is covered by the
-    tests)."""
+    FP64 atomics, pushes into private buffers plus a summing pass), and the
+    link gradient of Re <Y, Q_tm X> (tm_link_grad, the backward of the
+    autograd Q_tm), FP64 and FP32 storage (for information: correctness is
+    covered by the tests)."""
     from paper_1311_4521_gb300 import autograd
     dims = (24, 24, 24, 48)
     vh = int(np.prod(dims)) // 2
@@ -765,10 +766,20 @@ def grad_section(args, ctx, tmhop, torch, F) -> dict:
             fe[1].record(stream)
             torch.cuda.synchronize()
             sch_ms[name] = round(fe[0].elapsed_time(fe[1]) / 10, 4)
+        # the link gradient of Re <Y, Q_tm X> (the backward of autograd.qtm): two hops + the per-link kernel
+        yp = ctx.pack(phi, fprec)
+        lg = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ctx.link_grad(g, xp, yp, tmhop.TM_GRAD_QTM, KAPPA, MU)
+        lg[0].record(stream)
+        for _ in range(10):
+            ctx.link_grad(g, xp, yp, tmhop.TM_GRAD_QTM, KAPPA, MU)
+        lg[1].record(stream)
+        torch.cuda.synchronize()
         g.close()
         out[f"{inner}_solve_{fprec}_force"] = {
             "forward_s": round(e0.elapsed_time(e1) / 1e3, 4), "backward_s": round(e1.elapsed_time(e2) / 1e3, 4),
-            "force_ms": sch_ms["owner"], "force_ms_by_scheme": sch_ms, "S": float(S.item())}
+            "force_ms": sch_ms["owner"], "force_ms_by_scheme": sch_ms, "S": float(S.item()),
+            "link_grad_qtm_ms": round(lg[0].elapsed_time(lg[1]) / 10, 4)}
     return out
 
 

@@ -506,11 +506,19 @@ extern "C" tm_status tm_Qtm_batch(tm_ctx *ctx, int nsys, const tm_gauge *const *
     staged = staged && nrhs_max >= 2;
     cudaError_t e = cudaSuccess;
     if (staged) {
+        // the staged hop is an optional candidate: without memory for its link
+        // copies the batch runs with the gather hops alone
         for (auto *h : handles)
             if (e == cudaSuccess) e = stage_links8(h, s);
         if (e == cudaSuccess && !ctx->dev_status) {
             e = cudaMalloc(&ctx->dev_status, sizeof(int));
             if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), s);
+            else ctx->dev_status = nullptr;
+        }
+        if (e == cudaErrorMemoryAllocation) {
+            (void)cudaGetLastError();   // not sticky: clear it and go on without the staged hop
+            staged = false;
+            e = cudaSuccess;
         }
         if (e != cudaSuccess) return bcuda(ctx, e, "tm_Qtm_batch: staged-hop links");
     }
