@@ -124,6 +124,13 @@ tm_status tm_ctx_set_batch_config(tm_ctx *ctx, int code, unsigned cap);
  * flag is cleared by the check. */
 tm_status tm_ctx_check(tm_ctx *ctx);
 
+/* Test of the bounded-wait path: enqueues on `stream` one CTA whose thread
+ * waits on a shared-memory barrier that nothing completes.  The wait gives
+ * up after its limit (about a second), records that in the context's device
+ * status and the kernel returns; tm_ctx_check then reports TM_ERR_CUDA and
+ * clears it.  The context stays usable. */
+tm_status tm_ctx_selftest_wait(tm_ctx *ctx, void *stream);
+
 /* Text report of the launch configurations the context has chosen so far,
  * one line per batch shape: "<key> nrb=<pass width> cap=<CTA cap> ms3=<time
  * of three launches at selection> band=<1: tiles in z bands, t within a

@@ -187,4 +187,43 @@ bool stage_link_map(const tm_gauge *U, CUtensorMap &m)
     return U->links8 && encode(m, true, 5, U->links8, dims, str, box);
 }
 
+namespace {
+
+// One thread waits on a barrier that nothing arrives at: the wait runs out
+// after its limit and records that in *status (the path every staged-hop
+// wait takes when a copy never completes).
+__global__ void k_wait_selftest(int *status)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) (void)mbar_wait(b, 0, status);
+}
+
+}  // namespace
+
 }  // namespace twm
+
+using namespace twm;
+
+extern "C" tm_status tm_ctx_selftest_wait(tm_ctx *ctx, void *stream)
+{
+    if (!ctx) return TM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->dev_status) {
+        e = cudaMalloc(&ctx->dev_status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), s);
+        else ctx->dev_status = nullptr;
+    }
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, s>>>(ctx->dev_status);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return tm_fail(ctx, TM_ERR_CUDA, std::string("tm_ctx_selftest_wait: ") + cudaGetErrorString(e));
+    return TM_OK;
+}

@@ -92,6 +92,7 @@ def _load() -> ctypes.CDLL:
         "tm_Qnd": ([P, P, P, P, P, P, D, D, D, I, P], I),
         "tm_link_grad": ([P, P, P, P, P, I, D, D, I, P], I),
         "tm_ctx_check": ([P], I),
+        "tm_ctx_selftest_wait": ([P, P], I),
         "tm_clover_create": ([P, P, P, D, D, D, P, ctypes.POINTER(P)], I),
         "tm_clover_destroy": ([P], None),
         "tm_clover_bytes": ([P], S),
@@ -313,6 +314,11 @@ def tm_Qnd(ctx, U, out_s, out_c, in_s, in_c, kappa, mu_sigma, mu_delta, sign=1, 
 def tm_ctx_check(ctx):
     """Raises TmError if a bounded device wait of the context ran out since the last check."""
     _check(ctx, lib.tm_ctx_check(ctx))
+
+
+def tm_ctx_selftest_wait(ctx, stream=None):
+    """Enqueues the bounded-wait test kernel (a wait that runs out after about a second)."""
+    _check(ctx, lib.tm_ctx_selftest_wait(ctx, _stream(stream)))
 
 
 def tm_link_grad(ctx, U, G_dev, X_dev, Y_dev, op, kappa=0.0, mu=0.0, sign=1, stream=None):

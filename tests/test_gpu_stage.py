@@ -100,3 +100,20 @@ def test_staged_hop_boundary_signs(ctx, bc):
     the position in the box."""
     spec = [((32, 4, 4, 6), 2)]
     _run(ctx, "f32", 12, spec, 100, 2, 990, signs=(1,), bc=bc)
+
+
+def test_bounded_wait_runs_out_and_reports(ctx):
+    """A shared-memory barrier wait that nothing completes gives up after its
+    limit, the status reaches the host through tm_ctx_check (once: the check
+    clears it), and the context goes on working."""
+    import time
+
+    from paper_1311_4521_gb300 import tmhop
+    tmhop.tm_ctx_check(ctx.handle)   # nothing pending
+    t0 = time.perf_counter()
+    tmhop.tm_ctx_selftest_wait(ctx.handle)
+    with pytest.raises(tmhop.TmError):
+        tmhop.tm_ctx_check(ctx.handle)
+    assert time.perf_counter() - t0 < 30.0
+    tmhop.tm_ctx_check(ctx.handle)   # cleared
+    _run(ctx, "f32", 12, [((16, 2, 2, 4), 2)], 100, 0, 995, signs=(1,))
