@@ -477,12 +477,32 @@ def gpu_arm(args) -> None:
             "gflops": round(gflops, 2), "roofline": roofline, "fp64_probe": probe, "hbm_peak_gbs": hbm_peak,
             "hbm_peak_source": hbm_src,
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "nd_doublet": nd, "clover": sw, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "paper_context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# The paper's own figures on its hardware, as context (not targets, no
+# ratio): it prints its hopping-matrix and inverter throughput only in plots
+# that its text does not contain; these are the figures its prose states.
+PAPER_CONTEXT = {
+    "note": "figures stated in the text of arXiv:1311.4521 for its CPU machines; "
+            "its throughput plots are not in the text",
+    "items": [
+        {"what": "loss of the hop's floating-point rate from OpenMP threading (1 process x 64 threads "
+                 "against 64 processes per node, communication off)",
+         "value": "about 11 GFlop/s per node", "hardware": "IBM BlueGene/Q (JuQueen), 32 nodes, 12^4 sites per node",
+         "where": "Sec. 3"},
+        {"what": "gain from overlapping the halo exchange with the hop's body",
+         "value": "about 100 MFlop/s per core", "hardware": "Cray XC30 and SuperMUC", "where": "Sec. 2.5"},
+        {"what": "full-spinor hop with a precomputed neighbour-index order (g_hi) against "
+                 "two-dimensional neighbour tables",
+         "value": "almost 20 % faster", "hardware": "multi-core Intel CPUs", "where": "Sec. 2.2"},
+    ],
+}
 
 
 def nd_section(args, ctx, tmhop, torch, F, U, dims, vh, hbm_peak, allmax) -> dict:
