@@ -409,10 +409,11 @@ def gpu_arm(args) -> None:
             del sp, dp
 
     # ---- the non-degenerate twisted doublet (two flavours, links loaded once for both)
-    nd = sw = None
+    nd = sw = slabs = None
     if not args.no_table:
         nd = nd_section(args, ctx, tmhop, torch, F, U, DIMS, vh, hbm_peak, allmax)
         sw = clover_section(args, ctx, tmhop, torch, F, U, DIMS, vh, hbm_peak, allmax)
+        slabs = slab_section(args, ctx, tmhop, torch, F, U, DIMS, vh)
 
     # ---- CG on Q^dag Q to true relative residual 1e-10: FP64 vs mixed precision
     cg = None
@@ -476,7 +477,7 @@ def gpu_arm(args) -> None:
                               f"+ {tmhop.tm_spinor_bytes(vh, tmhop.PREC[prec]) / 1e9:.3f} GB spinor read per step), no flush"),
             "gflops": round(gflops, 2), "roofline": roofline, "fp64_probe": probe, "hbm_peak_gbs": hbm_peak,
             "hbm_peak_source": hbm_src,
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "nd_doublet": nd, "clover": sw, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": ck, "precisions": table, "nd_doublet": nd, "clover": sw, "slabs": slabs, "f64x_equivalent": f64x, "cg": cg, "batch": batch, "grad": grad,
             "cpu_baseline": cpu, "paper_context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)
@@ -546,6 +547,62 @@ def nd_section(args, ctx, tmhop, torch, F, U, dims, vh, hbm_peak, allmax) -> dic
         del ins, outs
     out["note"] = ("bytes per even site: launch A 2 x (in + out) + 8 links, launch B 2 x (in + out + x) + 8 links; "
                    "flops counted: the two flavours' hops (2 x 2 x 1320)")
+    return out
+
+
+def slab_section(args, ctx, tmhop, torch, F, U, dims, vh) -> dict:
+    """Q_tm on the workload lattice cut into n = 1, 2, 4 time slabs on this
+    one GPU (paper_1311_4521_gb300.slab.LocalSlabs: per hop, the faces are
+    packed, copied on a second stream while the interior runs, and the face
+    sites run last), FP64-18 and FP32-12, against the monolithic Q_tm: what
+    the surface/body split costs in launches and face traffic.  All slabs
+    run one after the other here, so `ms_per_slab` = ms / n is one slab's
+    share; across GPUs the slabs would run at once (not measured: one GPU)."""
+    from paper_1311_4521_gb300.slab import LocalSlabs
+    psi = F.gaussian_spinor(vh, F.SEED_PROD_32, 1)
+    stream = torch.cuda.current_stream()
+    out = {"note": "n slabs of one lattice on one GPU, run in turn; ms_per_slab = ms / n"}
+    reps = max(3, min(args.steps, 50))
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for prec, recon in (("f64", 18), ("f32", 12)):
+        g = ctx.gauge(dims, U, prec, recon)
+        src, dst = ctx.pack(psi, prec), ctx.empty(vh, prec)
+        mono = timed(lambda: ctx.Qtm(g, dst, src, KAPPA, MU))
+        g.close()
+        row = {"monolithic_ms": round(mono, 4)}
+        for n in (1, 2, 4):
+            sl = LocalSlabs(ctx, dims, U, n, prec, recon)
+            ins, outs = sl.pack_fields(psi), sl.empty()
+            ms = timed(lambda: sl.Qtm(outs, ins, KAPPA, MU))
+            entry = {"ms": round(ms, 4), "ms_per_slab": round(ms / n, 4),
+                     "overhead_vs_monolithic": round(ms / mono - 1.0, 4)}
+            # the same schedule captured once in a CUDA graph: without the
+            # per-call host submission of its 6n launches and 4n copies
+            try:
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    sl.Qtm(outs, ins, KAPPA, MU)
+                gms = timed(graph.replay)
+                entry.update({"graph_ms": round(gms, 4), "graph_overhead_vs_monolithic": round(gms / mono - 1.0, 4)})
+                del graph
+            except Exception as exc:   # capture is an extra measurement, not part of the schedule
+                entry["graph_ms"] = None
+                entry["graph_note"] = f"capture failed: {type(exc).__name__}"
+            sl.close()
+            row[f"{n}_slabs"] = entry
+        out[f"{prec}-{recon}"] = row
     return out
 
 
