@@ -34,7 +34,7 @@ struct BGroup {
 // again.  With bands of zband z planes the order is band, t, tile within the
 // band's slab, so the t neighbours are one band slab (a few thousand sites)
 // away; only the z neighbours across band edges are read twice.
-__device__ __forceinline__ unsigned tile_of(const BGroup &G, unsigned tno, unsigned ts)
+TM_HD unsigned tile_of(const BGroup &G, unsigned tno, unsigned ts)
 {
     if (G.zband == 0) return tno;
     const unsigned plane = unsigned(G.g.hx) * unsigned(G.g.ly);

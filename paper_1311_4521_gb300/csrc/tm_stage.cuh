@@ -242,7 +242,7 @@ __device__ __forceinline__ void stage_dir(const Nbrs &n, const StagedLinks<P, RE
 struct TileBox {
     int xh0, y0, z0, t0;
 };
-__device__ __forceinline__ TileBox tile_box(const Geom &g, int sbz, unsigned tno)
+TM_HD TileBox tile_box(const Geom &g, int sbz, unsigned tno)
 {
     const unsigned nbx = unsigned(g.hx) / SBX, nby = unsigned(g.ly) / 2, nbt = unsigned(g.lt) / 2;
     unsigned q = tno;
@@ -256,6 +256,52 @@ __device__ __forceinline__ TileBox tile_box(const Geom &g, int sbz, unsigned tno
     b.t0 = int(q % nbt) * 2;
     b.z0 = int((q / nbt) * unsigned(sbz) + zl) * 2;
     return b;
+}
+
+// Even-odd index of site s (0..63: x-half fastest, then y, z, t) of box B.
+TM_HD unsigned box_site_index(const Geom &g, const TileBox &B, int s)
+{
+    const int a = s & 7, b = (s >> 3) & 1, c = (s >> 4) & 1, d = s >> 5;
+    return ((unsigned(B.t0 + d) * unsigned(g.lz) + unsigned(B.z0 + c)) * unsigned(g.ly) + unsigned(B.y0 + b)) *
+               unsigned(g.hx) + unsigned(B.xh0 + a);
+}
+
+// Origin (x-half, y, z, t) of stage box b of tile B: the own box, or the
+// layer / column just outside it, wrapped onto the periodic lattice.
+struct BoxOrigin {
+    int x, y, z, t;
+};
+TM_HD BoxOrigin stage_box_origin(const Geom &g, const TileBox &B, int b)
+{
+    BoxOrigin o{B.xh0, B.y0, B.z0, B.t0};
+    if (b == B_XM) o.x = (B.xh0 - 1 + g.hx) % g.hx;
+    if (b == B_XP) o.x = (B.xh0 + SBX) % g.hx;
+    if (b == B_YM) o.y = (B.y0 - 1 + g.ly) % g.ly;
+    if (b == B_YP) o.y = (B.y0 + 2) % g.ly;
+    if (b == B_ZM) o.z = (B.z0 - 1 + g.lz) % g.lz;
+    if (b == B_ZP) o.z = (B.z0 + 2) % g.lz;
+    if (b == B_TM) o.t = (B.t0 - 1 + g.lt) % g.lt;
+    if (b == B_TP) o.t = (B.t0 + 2) % g.lt;
+    return o;
+}
+
+// Where the 8 neighbours of box site s (even-odd index i, neighbours n)
+// lie in the stage: q[2 mu] forward, q[2 mu + 1] backward.
+TM_HD void stage_neighbour_slots(const TileBox &B, int s, unsigned i, const Nbrs &n, SPos (&q)[8])
+{
+    const int a = s & 7, b = (s >> 3) & 1, c = (s >> 4) & 1, d = s >> 5;
+    const unsigned row = i - unsigned(B.xh0 + a);
+    const int af = n.wf[1] ? SBX : int(n.fwd[1] - row) - B.xh0;
+    const int ab = n.wb[1] ? -1 : int(n.bwd[1] - row) - B.xh0;
+    const int xcol = (d * 2 + c) * 2 + b;
+    q[0] = d == 0 ? SPos{B_OWN, s + 32} : SPos{B_TP, (c * 2 + b) * 8 + a};
+    q[1] = d == 1 ? SPos{B_OWN, s - 32} : SPos{B_TM, (c * 2 + b) * 8 + a};
+    q[2] = af >= SBX ? SPos{B_XP, xcol} : SPos{B_OWN, s - a + af};
+    q[3] = ab < 0 ? SPos{B_XM, xcol} : SPos{B_OWN, s - a + ab};
+    q[4] = b == 0 ? SPos{B_OWN, s + 8} : SPos{B_YP, (d * 2 + c) * 8 + a};
+    q[5] = b == 1 ? SPos{B_OWN, s - 8} : SPos{B_YM, (d * 2 + c) * 8 + a};
+    q[6] = c == 0 ? SPos{B_OWN, s + 16} : SPos{B_ZP, (d * 2 + b) * 8 + a};
+    q[7] = c == 1 ? SPos{B_OWN, s - 16} : SPos{B_ZM, (d * 2 + b) * 8 + a};
 }
 
 template <int P, int RECON, int MODE>
@@ -320,11 +366,7 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
             mbar_expect_tx(lfull(ls), C::LBYTES);
             tma_load5(smem_addr(ltiles + ls * C::LBYTES), sa.lmaps + gi, W * B.xh0, B.y0, B.z0, B.t0, parity * LCH,
                       lfull(ls));
-            const int hx = G.g.hx, ly = G.g.ly, lz = G.g.lz, lt = G.g.lt;
-            const int xm = (B.xh0 - 1 + hx) % hx, xp = (B.xh0 + SBX) % hx;
-            const int ym = (B.y0 - 1 + ly) % ly, yp = (B.y0 + 2) % ly;
-            const int zm = (B.z0 - 1 + lz) % lz, zp = (B.z0 + 2) % lz;
-            const int tm = (B.t0 - 1 + lt) % lt, tp = (B.t0 + 2) % lt;
+            const int hx = G.g.hx;
             for (int r = 0; r < G.nrhs; ++r) {
                 if (gated(sys[G.sys0 + r].s, gate)) continue;
                 const int slot = int(u % C::NSTAGE);
@@ -336,15 +378,13 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
                 const CUtensorMap *m = sa.smaps + (size_t(G.sys0 + r) * NROLE + rin) * (2 * NSH);
 #pragma unroll
                 for (int b = 0; b < NBOX; ++b) {
-                    const int x = b == B_XM ? xm : b == B_XP ? xp : B.xh0;
-                    const int y = b == B_YM ? ym : b == B_YP ? yp : B.y0;
-                    const int z = b == B_ZM ? zm : b == B_ZP ? zp : B.z0;
-                    const int t = b == B_TM ? tm : b == B_TP ? tp : B.t0;
-                    tma_load5(smem_addr(st + box_first(b) * C::CH * 16), m + box_shape(b), 2 * x, y, z, t, 0, fb);
+                    const BoxOrigin o = stage_box_origin(G.g, B, b);
+                    tma_load5(smem_addr(st + box_first(b) * C::CH * 16), m + box_shape(b), 2 * o.x, o.y, o.z, o.t, 0,
+                              fb);
                     if constexpr (C::CH == 3) {   // FP16 site norms; x columns 4 wide at 16-byte boundaries
-                        const int xn = b == B_XM ? (B.xh0 - 4 + hx) % hx : x;
-                        tma_load4(smem_addr(st + C::NORM_OFF + nbox_first(b) * 4), m + NSH + box_shape(b), xn, y, z, t,
-                                  fb);
+                        const int xn = b == B_XM ? (B.xh0 - 4 + hx) % hx : o.x;
+                        tma_load4(smem_addr(st + C::NORM_OFF + nbox_first(b) * 4), m + NSH + box_shape(b), xn, o.y,
+                                  o.z, o.t, fb);
                     }
                 }
                 ++u;
@@ -357,7 +397,6 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
     // ---------------- consumers: group warp/2 computes the stages j = group (mod NG)
     const int grp = warp >> 1;
     const int s = (warp & 1) * 32 + lane;   // site of the box
-    const int a = s & 7, b = (s >> 3) & 1, c = (s >> 4) & 1, d = s >> 5;
     unsigned u = 0, tl = 0;
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
         const BGroup &G = groups[find_group(groups, ngroups, staged, item)];
@@ -367,8 +406,7 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
         const TileBox B = tile_box(G.g, G.sbz, item - G.item0);
         const int ls = int(tl & 1);
         const unsigned vh = G.g.vh;
-        const unsigned i = ((unsigned(B.t0 + d) * unsigned(G.g.lz) + unsigned(B.z0 + c)) * unsigned(G.g.ly) +
-                            unsigned(B.y0 + b)) * unsigned(G.g.hx) + unsigned(B.xh0 + a);
+        const unsigned i = box_site_index(G.g, B, s);
         Nbrs n;
         neighbours(G.g, parity, i, n);
         unsigned neg = 0;
@@ -377,19 +415,8 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
             if (G.g.anti[mu] && n.wf[mu]) neg |= 1u << mu;
             if (G.g.anti[mu] && n.wb[mu]) neg |= 16u << mu;
         }
-        // positions of the 8 neighbours in the stage
-        const unsigned row = i - unsigned(B.xh0 + a);
-        const int af = n.wf[1] ? SBX : int(n.fwd[1] - row) - B.xh0;
-        const int ab = n.wb[1] ? -1 : int(n.bwd[1] - row) - B.xh0;
-        const int xcol = (d * 2 + c) * 2 + b;
-        const SPos q0f = d == 0 ? SPos{B_OWN, s + 32} : SPos{B_TP, (c * 2 + b) * 8 + a};
-        const SPos q0b = d == 1 ? SPos{B_OWN, s - 32} : SPos{B_TM, (c * 2 + b) * 8 + a};
-        const SPos q1f = af >= SBX ? SPos{B_XP, xcol} : SPos{B_OWN, s - a + af};
-        const SPos q1b = ab < 0 ? SPos{B_XM, xcol} : SPos{B_OWN, s - a + ab};
-        const SPos q2f = b == 0 ? SPos{B_OWN, s + 8} : SPos{B_YP, (d * 2 + c) * 8 + a};
-        const SPos q2b = b == 1 ? SPos{B_OWN, s - 8} : SPos{B_YM, (d * 2 + c) * 8 + a};
-        const SPos q3f = c == 0 ? SPos{B_OWN, s + 16} : SPos{B_ZP, (d * 2 + b) * 8 + a};
-        const SPos q3b = c == 1 ? SPos{B_OWN, s - 16} : SPos{B_ZM, (d * 2 + b) * 8 + a};
+        SPos q[8];   // positions of the 8 neighbours in the stage
+        stage_neighbour_slots(B, s, i, n, q);
         const StagedLinks<P, C::LRECON> src{reinterpret_cast<const V *>(ltiles + ls * C::LBYTES), STS, unsigned(s)};
         if (!mbar_wait(lfull(ls), (tl >> 1) & 1, sa.status)) return;
         const int nrhs = G.nrhs, sys0 = G.sys0;
@@ -410,10 +437,10 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) acc[sp][cc] = {R(0), R(0)};
-            stage_dir<P, C::LRECON, 0>(n, src, st, q0f, q0b, neg, acc);
-            stage_dir<P, C::LRECON, 1>(n, src, st, q1f, q1b, neg, acc);
-            stage_dir<P, C::LRECON, 2>(n, src, st, q2f, q2b, neg, acc);
-            stage_dir<P, C::LRECON, 3>(n, src, st, q3f, q3b, neg, acc);
+            stage_dir<P, C::LRECON, 0>(n, src, st, q[0], q[1], neg, acc);
+            stage_dir<P, C::LRECON, 1>(n, src, st, q[2], q[3], neg, acc);
+            stage_dir<P, C::LRECON, 2>(n, src, st, q[4], q[5], neg, acc);
+            stage_dir<P, C::LRECON, 3>(n, src, st, q[6], q[7], neg, acc);
             __syncwarp();
             if (lane == 0) mbar_arrive(empty(slot));   // the stage may be refilled
             Spinor<R> o;

@@ -28,3 +28,21 @@ def test_site_maps_cover_every_site_once(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout + out.stderr
     assert "0 failures" in out.stdout
+
+
+def test_batched_work_orders_and_stage_slots(tmp_path):
+    """The batched hops' work orders on the host: the banded tile order is a
+    permutation of the tiles, the staged hop's boxes cover every site once,
+    and every stage slot a consumer reads holds the neighbour it wants, by
+    the content the producer's tensor copies put there (12 lattice shapes,
+    both output parities, including 32^3x64)."""
+    nvcc = _nvcc()
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    include = os.path.join(os.path.dirname(HERE), "include")
+    exe = tmp_path / "tile_order_check"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "--expt-relaxed-constexpr", "-I", CSRC, "-I", include,
+                    os.path.join(HERE, "host", "tile_order_check.cu"), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.strip().endswith("OK"), out.stdout
