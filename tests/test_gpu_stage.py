@@ -117,3 +117,29 @@ def test_bounded_wait_runs_out_and_reports(ctx):
     assert time.perf_counter() - t0 < 30.0
     tmhop.tm_ctx_check(ctx.handle)   # cleared
     _run(ctx, "f32", 12, [((16, 2, 2, 4), 2)], 100, 0, 995, signs=(1,))
+
+
+@pytest.mark.parametrize("code", [-1, 100])
+def test_batched_qtm_12rhs_full_size(ctx, code):
+    """The benchmark's batching workload, 12 right-hand sides on 32^3x64 in
+    FP32-12 storage, in the configuration the bench times (the tuned one)
+    and with the TMA-staged hop forced: every right-hand side against the
+    oracle's FP64 Q_tm."""
+    from paper_1311_4521_gb300 import tmhop
+    dims = (32, 32, 32, 64)
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, F.SEED_PROD_32, "near", 0.3)
+    g = ctx.gauge(dims, U, "f32", 12)
+    rhs = [F.gaussian_spinor(vh, F.SEED_BATCH_RHS + j, 0) for j in range(12)]
+    ins = [ctx.pack(r, "f32") for r in rhs]
+    outs = [ctx.empty(vh, "f32") for _ in rhs]
+    try:
+        tmhop.tm_ctx_set_batch_config(ctx.handle, code, 0)
+        ctx.Qtm_batch([g] * 12, outs, ins, 0.1394, 0.0015)
+        tmhop.tm_ctx_check(ctx.handle)
+        for r, o in zip(rhs, outs):
+            want = O.Qtm(dims, U, r, 0.1394, 0.0015)
+            assert rel(ctx.unpack(o, vh, "f32").cpu().numpy(), want) < TOL["f32"]
+    finally:
+        tmhop.tm_ctx_set_batch_config(ctx.handle, -1, 0)
+        g.close()
