@@ -164,3 +164,34 @@ def test_autograd_hopping_link_gradient(ctx, direction):
         fd = (loss(U + eps * D) - loss(U - eps * D)) / (2 * eps)   # exact: the loss is quadratic in U
         got = np.sum(np.conj(G) * D).real
         assert abs(got - fd) <= 1e-11 * (np.linalg.norm(G) * np.linalg.norm(D) + abs(fd))
+
+
+def test_link_grad_qtm_full_size(ctx):
+    """The configuration the bench times (24^3x48, FP64-18, U = exp(0.3 i A)):
+    the gradient along single links (bulk, and across the antiperiodic time
+    boundary) and along one dense direction against the oracle's central
+    differences, which are exact for Q_tm (quadratic in U)."""
+    from paper_1311_4521_gb300 import tmhop
+    dims = (24, 24, 24, 48)
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, F.SEED_GRAD_24, "near", 0.3)
+    X = F.gaussian_spinor(vh, F.SEED_GRAD_24, 1)
+    Y = F.gaussian_spinor(vh, F.SEED_GRAD_24, 2)
+    g = ctx.gauge(dims, U, "f64", 18)
+    G = ctx.link_grad(g, ctx.pack(X, "f64"), ctx.pack(Y, "f64"), tmhop.TM_GRAD_QTM, KAPPA, MU).cpu().numpy()
+    g.close()
+    f = lambda W: np.vdot(Y.reshape(-1), O.Qtm(dims, W, X, KAPPA, MU).reshape(-1)).real
+    rng = np.random.default_rng(17)
+    Lx, Ly, Lz, Lt = dims
+    lex = lambda x, y, z, t: x + Lx * (y + Ly * (z + Lz * t))
+    dirs = []
+    for mu, site in ((0, lex(3, 5, 7, Lt - 1)), (0, lex(10, 2, 19, 20)), (1, lex(Lx - 1, 4, 4, 4)), (3, lex(1, 2, 3, 0))):
+        D = np.zeros(U.shape, dtype=np.complex128)
+        D[mu, site] = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        dirs.append(D)
+    dirs.append(rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape))
+    eps = 1e-3
+    for D in dirs:
+        fd = (f(U + eps * D) - f(U - eps * D)) / (2 * eps)
+        got = np.sum(np.conj(G) * D).real
+        assert abs(got - fd) <= 1e-10 * (np.linalg.norm(G) * np.linalg.norm(D) + abs(fd)), (got, fd)
