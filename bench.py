@@ -380,7 +380,11 @@ def gpu_arm(args) -> None:
         nbytes = host_in.numel() * 16
         e2e = {"value": round(world * vh * ab["qtm"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e2e_ms, 4),
-               "steps": ne, "gpu_launches_per_step": 4, "api": "tm_Qtm_host (pinned host fields, pipelined copies)"}
+               "steps": ne,
+               # FP64: the two hops read and write the canonical host layout themselves; other formats add
+               # a pack and an unpack launch per field
+               "gpu_launches_per_step": 2 if prec == "f64" else 4,
+               "api": "tm_Qtm_host (pinned host fields, pipelined copies)"}
         del host_in, host_out
     links_gb = tmhop.tm_gauge_bytes(g.handle) / 1e9
     g.close()

@@ -57,6 +57,10 @@ namespace twm {
 // FP64 value stored as a double-float pair (FP32 hi, lo) and computed on with
 // double-float arithmetic (tm_dd.cuh).
 enum { F64 = 0, F32 = 1, F16 = 2, F64X = 3 };
+// Not a storage format of a handle: FP64 spinors in the caller's canonical
+// layout ([site][spin][colour] complex double), read and written in place by
+// the host-field operator (tm_Qtm_host) instead of being packed first.
+enum { F64C = 4 };
 
 // Conversions between double and the compute type of a storage precision.
 template <typename R> TM_HD R to_R(double x) { return R(x); }
@@ -331,6 +335,31 @@ template <> struct SpinorIO<F32> {
             const cpx<R> &c = s[(2 * k + 1) / 3][(2 * k + 1) % 3];
             st_stream(b + size_t(k) * vh + i, make_float4(a.re, a.im, c.re, c.im));
         }
+    }
+};
+
+// The canonical layout: site i's 12 complex components at [12 i, 12 i + 12).
+template <> struct SpinorIO<F64C> {
+    using R = double;
+    TM_HD static R load_raw(const void *base, unsigned vh, unsigned i, Spinor<R> &s)
+    {
+        load(base, vh, i, s);
+        return R(1);
+    }
+    TM_HD static void load(const void *base, unsigned, unsigned i, Spinor<R> &s)
+    {
+        const double2 *b = static_cast<const double2 *>(base) + size_t(i) * 12;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 v = ld_keep(b + c);
+            s[c / 3][c % 3] = {v.x, v.y};
+        }
+    }
+    TM_HD static void store(void *base, unsigned, unsigned i, const Spinor<R> &s)
+    {
+        double2 *b = static_cast<double2 *>(base) + size_t(i) * 12;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) st_stream(b + c, make_double2(s[c / 3][c % 3].re, s[c / 3][c % 3].im));
     }
 };
 
@@ -994,7 +1023,7 @@ TM_HD void hop_site_src(const Geom &g, const Nbrs &n, const Src &src, const void
         for (int c = 0; c < 3; ++c) acc[s][c] = {R(0), R(0)};
     if constexpr (P == F64X) {
         hop_site_rolled<P, DAG>(g, n, src, in, acc);
-    } else if constexpr (P == F64) {
+    } else if constexpr (P == F64 || P == F64C) {
         hop_dir_pair<P, DAG, 0, true>(g, n, src, in, acc);
         hop_dir_pair<P, DAG, 1, false>(g, n, src, in, acc);
         hop_dir_pair<P, DAG, 2, false>(g, n, src, in, acc);

@@ -7,10 +7,12 @@
 // fields and pipelines them through two device staging slots: while the
 // operator of field k runs on the compute stream, field k+1 is copied in
 // and packed on one copy stream and field k-1 unpacked and copied out on
-// another.  The operator in FP64 is bound by the FP64 units and leaves most
-// of the memory bandwidth free, so the memory-bound pack and unpack kernels
-// and, with pinned host memory, the copies hide behind it.  Every copy is
-// one cudaMemcpyAsync of one contiguous field.
+// another.  For FP64 handles the operator's two launches read the input
+// and write the result in the caller's canonical layout directly (the
+// component-major packing only pays for itself when a field is used many
+// times), so only the copies run beside it; the other formats pack and
+// unpack on the copy streams.  Every copy is one cudaMemcpyAsync of one
+// contiguous field.
 #include <set>
 #include <string>
 
@@ -103,7 +105,38 @@ extern "C" tm_status tm_Qtm_host(tm_ctx *ctx, const tm_gauge *U, int n, double *
 
     cudaStream_t s = (cudaStream_t)stream, ci = ctx->copy_in, co = ctx->copy_out;
     st = TM_OK;
-    for (int k = 0; k < n && e == cudaSuccess && st == TM_OK; ++k) {
+    if (U->prec == F64) {
+        // FP64: the operator reads and writes the canonical staging slots
+        // itself (no pack or unpack launches competing with it for the SMs).
+        // Events per slot: packed = copied in, unpacked = copied out.
+        const double mut = 2.0 * kappa * mu * sign;
+        const Coef ka = coef_qtm_a_scaled(kappa, mut), kb = coef_qtm_b_unit(mut);
+        for (int k = 0; k < n && e == cudaSuccess; ++k) {
+            const int q = k & 1;
+            // copy-in stream: once the operator of field k-2 has read this slot, field k
+            e = cudaStreamWaitEvent(ci, ev.multiplied[q], 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(can_in[q], in_host[k], cb, cudaMemcpyHostToDevice, ci);
+            if (e == cudaSuccess) e = cudaEventRecord(ev.packed[q], ci);
+            // compute stream: once field k is in and field k-2's result has left the slot
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.packed[q], 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.unpacked[q], 0);
+            if (e == cudaSuccess) {
+                tm_trace_mark(ctx, 0, s);
+                e = launch_qtm_canonical(false, U->geom, U->recon, U->map, U->links, can_in[q], tmp, can_out[q], ka, s);
+                tm_trace_mark(ctx, 1, s);
+                if (e == cudaSuccess)
+                    e = launch_qtm_canonical(true, U->geom, U->recon, U->map, U->links, can_in[q], tmp, can_out[q], kb,
+                                             s);
+                tm_trace_mark(ctx, 2, s);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev.multiplied[q], s);
+            // copy-out stream: field k back to the host
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(co, ev.multiplied[q], 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(out_host[k], can_out[q], cb, cudaMemcpyDeviceToHost, co);
+            if (e == cudaSuccess) e = cudaEventRecord(ev.unpacked[q], co);
+        }
+    }
+    for (int k = 0; U->prec != F64 && k < n && e == cudaSuccess && st == TM_OK; ++k) {
         const int q = k & 1;
         // copy-in stream: field k to the device, then (once the operator of
         // field k-2 has read this slot's packed input) its pack

@@ -116,6 +116,11 @@ namespace twm {
 bool make_geom(const int dims[4], const int bc[4], Geom &g);
 
 // Launchers (tm_kernels.cu).  All enqueue on `s` and return the launch status.
+// Q_tm of an FP64 handle on fields in the canonical layout: launch A
+// (in_can -> tmp, an odd packed FP64 field) or launch B (tmp -> out_can,
+// in_can re-read), with coefficients k.
+cudaError_t launch_qtm_canonical(bool stage_b, const Geom &g, int recon, const SiteMap &m, const void *links,
+                                 const double *in_can, void *tmp, double *out_can, const Coef &k, cudaStream_t s);
 // The hop with the given site-to-thread map, or with the linear map of
 // `block` threads per CTA.
 cudaError_t launch_hop(const Geom &g, int prec, int recon, bool dag, int out_parity, const void *links,

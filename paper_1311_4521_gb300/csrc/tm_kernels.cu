@@ -83,6 +83,54 @@ __global__ void __launch_bounds__(128, TM_HOP_MINB(P)) k_hop(Geom g, int p, cons
     SpinorIO<P>::store(out, g.vh, i, o);
 }
 
+// The two Q_tm launches of tm_Qtm_host for FP64 handles, on the caller's
+// canonical layout: launch A (PI = F64C) gathers its input from it, launch B
+// re-reads it as x (PX = F64C) and writes its result in it (PO = F64C); the
+// odd temporary between them stays component-major.  The per-site
+// arithmetic is the hop's, so results equal tm_Qtm's on packed fields.
+template <int PI, int PX, int PO, int RECON, bool HASX>
+__global__ void __launch_bounds__(128, TM_HOP_MINB(F64))
+    k_hop_io(Geom g, int p, const typename LinkIO<F64, RECON>::V *__restrict__ links, const void *__restrict__ in,
+             void *__restrict__ out, const void *__restrict__ x, Coef k, SiteMap m)
+{
+    const unsigned i = map_site(g, m, blockIdx.x, threadIdx.x);
+    if (i >= g.vh) return;
+    Nbrs n;
+    neighbours(g, p, i, n);
+    GlobalLinks<F64, RECON> src{links, g.vh, i, p};
+    Spinor<double> acc, o;
+    hop_site_src<PI, false>(g, n, src, in, acc);
+    if (HASX) {
+        Spinor<double> xs;
+        SpinorIO<PX>::load(x, g.vh, i, xs);
+        epilogue(k, acc, &xs, o);
+    } else {
+        epilogue(k, acc, static_cast<const Spinor<double> *>(nullptr), o);
+    }
+    SpinorIO<PO>::store(out, g.vh, i, o);
+}
+
+template <int RECON>
+static cudaError_t qtm_canonical(bool stage_b, const Geom &g, const SiteMap &m, const void *links,
+                                 const double *in_can, void *tmp, double *out_can, const Coef &k, cudaStream_t s)
+{
+    using V = typename LinkIO<F64, RECON>::V;
+    const V *l = static_cast<const V *>(links);
+    const unsigned grid = map_grid(g, m);
+    if (!stage_b) k_hop_io<F64C, F64, F64, RECON, false><<<grid, m.block, 0, s>>>(g, 1, l, in_can, tmp, nullptr, k, m);
+    else k_hop_io<F64, F64C, F64C, RECON, true><<<grid, m.block, 0, s>>>(g, 0, l, tmp, out_can, in_can, k, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qtm_canonical(bool stage_b, const Geom &g, int recon, const SiteMap &m, const void *links,
+                                 const double *in_can, void *tmp, double *out_can, const Coef &k, cudaStream_t s)
+{
+    if (g.vh == 0) return cudaSuccess;
+    if (recon == 18) return qtm_canonical<18>(stage_b, g, m, links, in_can, tmp, out_can, k, s);
+    if (recon == 12) return qtm_canonical<12>(stage_b, g, m, links, in_can, tmp, out_can, k, s);
+    return cudaErrorInvalidValue;
+}
+
 template <int P, int RECON>
 static cudaError_t hop_dispatch(const Geom &g, bool dag, int p, const void *links, const void *in, void *out,
                                 const void *x, const Coef &k, cudaStream_t s, const SiteMap &m)
