@@ -143,10 +143,14 @@ size_t tm_ctx_tune_report(const tm_ctx *ctx, char *buf, size_t size);
 
 /* File in which tm_gauge_tune keeps its choices, one line "<key> <map>
  * <ms>" per lattice, keyed by "<GPU name>|<Lx>x<Ly>x<Lz>x<Lt>|prec<p>|recon<r>
- * |nrhs1" (NULL or "": no file).  A context starts with the path in the
+ * |nrhs1" (NULL or "": no file).  The batched hop (tm_Qtm_batch,
+ * tm_cg_QdagQ_batch) keeps its tuned configuration there too, one line
+ * "<GPU name>|bhop/<prec>/<recon>/<Vh>x<nrhs>[/...][/staged] code<c>-cap<n>
+ * <ms>" per batch shape.  A context starts with the path in the
  * environment variable TMHOP_TUNE_CACHE, if set.  With a cache file and
  * autotuning on, tm_gauge_create gives a new handle the cached map of its
- * lattice. */
+ * lattice and a batch whose shape has an entry runs its configuration
+ * without timing candidates. */
 tm_status tm_ctx_set_tune_cache(tm_ctx *ctx, const char *path);
 
 /* ---- fields --------------------------------------------------------------- */

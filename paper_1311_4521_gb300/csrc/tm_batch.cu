@@ -387,6 +387,23 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     }
     if (sa) key += "/staged";
     auto it = ctx->tuned.find(key);
+    // a choice persisted by an earlier process (tm_ctx_set_tune_cache), if its code is a candidate here
+    const std::string ckey = tune_cache_gpu(ctx) + "|" + key;
+    if (it == ctx->tuned.end() && ctx->autotune && !ctx->tune_cache.empty()) {
+        std::string val;
+        double cms = 0;
+        int code = -1;
+        unsigned cap = 0;
+        if (tune_cache_lookup(ctx->tune_cache, ckey, val, cms) && sscanf(val.c_str(), "code%d-cap%u", &code, &cap) == 2) {
+            const std::vector<int> ok = nrb_candidates(prec, recon, nrhs_max, sa != nullptr);
+            if (std::find(ok.begin(), ok.end(), code) != ok.end() && cap > 0) {
+                ctx->tuned[key] = {code, cap};
+                ctx->tuned_ms[key] = float(cms);
+                ctx->tuned_band[key] = band_order(prec) ? 1 : 0;
+                it = ctx->tuned.find(key);
+            }
+        }
+    }
     if (it != ctx->tuned.end()) {
         cudaError_t e = build_table(tmpl, it->second.first, it->second.second, out, dev, st, host, sta,
                                     band_order(prec));
@@ -421,6 +438,9 @@ cudaError_t tune_hop_table(tm_ctx *ctx, int prec, int recon, const std::vector<B
     ctx->tuned[key] = {best_nrb, best_cap};
     ctx->tuned_ms[key] = best;
     ctx->tuned_band[key] = band_order(prec) ? 1 : 0;
+    if (ctx->autotune && !ctx->tune_cache.empty())
+        tune_cache_store(ctx->tune_cache, ckey, "code" + std::to_string(best_nrb) + "-cap" + std::to_string(best_cap),
+                         best);
     cudaError_t e = build_table(tmpl, best_nrb, best_cap, out, dev, st, host, sta, band_order(prec));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;

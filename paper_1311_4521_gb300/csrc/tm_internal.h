@@ -111,6 +111,14 @@ struct tm_gauge {
 void tm_apply_cached_map(tm_ctx *ctx, tm_gauge *U);
 
 namespace twm {
+// The tune cache file (tm_tune.cu): lines "<key> <value> <ms>", the last
+// entry of a key wins; keys start with the GPU's name.
+std::string tune_cache_gpu(const tm_ctx *ctx);
+bool tune_cache_lookup(const std::string &path, const std::string &key, std::string &value, double &ms);
+void tune_cache_store(const std::string &path, const std::string &key, const std::string &value, double ms);
+}  // namespace twm
+
+namespace twm {
 
 // Fills the geometry of a lattice; returns false if the extents are invalid.
 bool make_geom(const int dims[4], const int bc[4], Geom &g);

@@ -147,6 +147,22 @@ float time_map(const tm_gauge *U, const SiteMap &m, const void *in, void *out, c
 
 }  // namespace
 
+namespace twm {
+
+std::string tune_cache_gpu(const tm_ctx *ctx) { return gpu_name(ctx->device); }
+
+bool tune_cache_lookup(const std::string &path, const std::string &key, std::string &value, double &ms)
+{
+    return cache_lookup(path, key, value, ms);
+}
+
+void tune_cache_store(const std::string &path, const std::string &key, const std::string &value, double ms)
+{
+    cache_store(path, key, value, ms);
+}
+
+}  // namespace twm
+
 // Applies the cached map of U's lattice, if the context has a cache file
 // with an entry for it (called by tm_gauge_create).
 void tm_apply_cached_map(tm_ctx *ctx, tm_gauge *U)

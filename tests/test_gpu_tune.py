@@ -114,3 +114,38 @@ def test_tune_persists_in_the_cache_file(tmp_path):
     for g, c in ((g1, c1), (g2, c2), (g3, c3)):
         g.close()
         c.close()
+
+
+def test_batched_choice_persists_in_the_cache_file(tmp_path):
+    """The batched hop's tuned configuration goes to the same cache file,
+    keyed by GPU, storage and the batch's (Vh x nrhs) groups; a new context
+    with that file takes it without timing (no second line) and computes the
+    same result, which matches the oracle."""
+    from paper_1311_4521_gb300 import tmhop
+    dims = (16, 8, 8, 8)
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, 404, "near", 0.3)
+    psis = [F.gaussian_spinor(vh, 404, 1 + j) for j in range(4)]
+    cache = tmp_path / "tune.txt"
+    outs, reports = [], []
+    for _ in range(2):
+        c = tmhop.Context(0)
+        tmhop.tm_ctx_set_tune_cache(c.handle, str(cache))
+        g = c.gauge(dims, U, "f32", 12)
+        ins = [c.pack(p, "f32") for p in psis]
+        o = [c.empty(vh, "f32") for _ in psis]
+        c.Qtm_batch([g] * 4, o, ins, 0.1394, 0.0015)
+        outs.append([c.unpack(t, vh, "f32").cpu().numpy() for t in o])
+        reports.append([ln for ln in tmhop.tm_ctx_tune_report(c.handle).splitlines() if ln.startswith("bhop/")])
+        g.close()
+        c.close()
+    lines = [ln for ln in cache.read_text().splitlines() if "|bhop/" in ln]
+    assert len(lines) == 1, lines
+    assert f"{vh}x4" in lines[0] and lines[0].split()[1].startswith("code")
+    nrb, cap = lines[0].split()[1][len("code"):].split("-cap")
+    for rep in reports:
+        assert any(f"nrb={nrb} cap={cap}" in ln for ln in rep), rep
+    for a, b, p in zip(outs[0], outs[1], psis):
+        assert np.array_equal(a, b)
+        want = O.Qtm(dims, U, p, 0.1394, 0.0015)
+        assert np.linalg.norm(a - want) / np.linalg.norm(want) < 1e-6
