@@ -747,8 +747,8 @@ def only_section(args, ctx, tmhop, torch, F, U, psi, dims, vh, barrier, allmax) 
         tmhop.tm_clover_destroy(C)
         g.close()
     elif args.only == "batch-qtm":
-        tmhop.tm_ctx_set_batch_config(ctx.handle, args.batch_code, 0)
-        res["batch_code"] = args.batch_code
+        tmhop.tm_ctx_set_batch_config(ctx.handle, args.batch_code, args.batch_cap)
+        res["batch_code"], res["batch_cap"] = args.batch_code, args.batch_cap
         g = ctx.gauge(dims, U, args.prec, args.recon)
         ins = [ctx.pack(F.gaussian_spinor(vh, F.SEED_BATCH_RHS + j, 0), args.prec) for j in range(12)]
         outs = [ctx.empty(vh, args.prec) for _ in range(12)]
@@ -1078,6 +1078,8 @@ def main() -> None:
                     help="run one section alone (for profiling captures)")
     ap.add_argument("--batch-code", type=int, default=-1,
                     help="batched-hop configuration for --only batch-qtm (-1: autotuned; 100: TMA-staged)")
+    ap.add_argument("--batch-cap", type=int, default=0,
+                    help="persistent CTA cap with --batch-code (0: one CTA per work item; code 100: one per SM)")
     ap.add_argument("--cg-delta", type=float, default=-1.0,
                     help="reliable-update threshold of the mixed-precision solvers (residual drop factor); "
                          "negative: the library's automatic choice (FP32 1e-3, FP16 0.022)")
