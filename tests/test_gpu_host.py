@@ -26,7 +26,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 2, 10)])
-@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64x", 18), ("f32", 12), ("f16", 12)])
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("f64x", 18), ("f32", 12), ("f16", 12)])
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_fields_match_oracle(ctx, dims, prec, recon, pinned):
     vh = int(np.prod(dims)) // 2
@@ -45,6 +45,28 @@ def test_host_fields_match_oracle(ctx, dims, prec, recon, pinned):
     dev = ctx.empty(vh, prec)
     ctx.Qtm(g, dev, ctx.pack(psis[3], prec), 0.1394, 0.0015, -1)
     assert np.array_equal(ctx.unpack(dev, vh, prec).cpu().numpy(), outs[3].numpy())
+    g.close()
+
+
+@pytest.mark.parametrize("map_name", ["box4x2x2x2", "linear64"])
+def test_host_fields_with_a_site_map(ctx, map_name):
+    """FP64 host fields go through the hops' canonical-layout launches with the
+    handle's site map: the same bits as tm_Qtm on packed fields with that map."""
+    from paper_1311_4521_gb300 import tmhop
+    dims = (8, 8, 8, 8)
+    vh = int(np.prod(dims)) // 2
+    U = F.gauge_field(dims, 23, "near", 0.3)
+    psis = [F.gaussian_spinor(vh, 23, k) for k in range(3)]
+    g = ctx.gauge(dims, U, "f64", 18)
+    tmhop.tm_gauge_set_map(ctx.handle, g.handle, map_name)
+    ins = [torch.from_numpy(p.copy()).pin_memory() for p in psis]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    ctx.Qtm_host(g, outs, ins, 0.1394, 0.0015)
+    for p, o in zip(psis, outs):
+        dev = ctx.empty(vh, "f64")
+        ctx.Qtm(g, dev, ctx.pack(p, "f64"), 0.1394, 0.0015)
+        assert np.array_equal(ctx.unpack(dev, vh, "f64").cpu().numpy(), o.numpy())
+        assert rel(o.numpy(), O.Qtm(dims, U, p, 0.1394, 0.0015)) < 1e-13
     g.close()
 
 
