@@ -61,8 +61,9 @@ def fp64_nominal_tflops(sm_count: int, sm_mhz: float) -> float:
 # another lattice scales by its site count), valid only for the kernel
 # sources they were taken from (hash of csrc/tm_device.cuh +
 # csrc/tm_kernels.cu).
-TRAFFIC = {"src": "3be4444c6e1f0cb8",
-           "per_site": {("f64", 18): 1791248128 / 1048576, ("f64x", 18): 1790081792 / 1048576, ("f32", 12): 689401344 / 1048576, ("f16", 12): 338128128 / 1048576}}
+TRAFFIC = {"src": "4d1e82678e27f879",
+           "per_site": {("f64", 18): 1790570752 / 1048576, ("f64x", 18): 1790290944 / 1048576,
+                        ("f32", 12): 678930688 / 1048576, ("f16", 12): 341252096 / 1048576}}
 
 
 def kernel_source_hash() -> str:
