@@ -58,15 +58,26 @@ template <> struct StageFmt<F32> {
     static constexpr int CH = 6;  // 16-byte components per site
     static constexpr int NORM = 0;
 };
+// FP16 site norms: staged like the components (0: nine more tensor copies per
+// stage, for 1280 bytes) or read by the consumers from memory (1, the
+// default: one 4-byte load per neighbour, issued before the stage is waited
+// for).  The single producer thread is on the critical path, so the nine
+// copies cost more than the loads: launch B 1.40 -> 1.13 ms on 32^3x64 with
+// 12 right-hand sides (and six consumer groups, which the smaller stages fit).
+#ifndef TM_STAGE_F16_NORM_GLOBAL
+#define TM_STAGE_F16_NORM_GLOBAL 1
+#endif
 template <> struct StageFmt<F16> {
     static constexpr int CH = 3;
-    static constexpr int NORM = 1;
+    static constexpr int NORM = TM_STAGE_F16_NORM_GLOBAL ? 0 : 1;
 };
 
 // Consumer groups and stage buffers per group (one computed on, the others
 // filling) of the FP32 and FP16 formats.  Measured on 32^3x64 with 12
-// right-hand sides: FP16 launch B 1.65, 1.39, 1.49, 1.55 ms with 2, 3, 4, 6
-// groups; FP32 is held to 3 groups of two stages by shared memory.
+// right-hand sides, FP16 launch B: with staged norms 1.65, 1.39, 1.49, 1.55
+// ms for 2, 3, 4, 6 groups; with norms from memory 1.38 (3 groups of 2
+// stages), 1.20 (4 of 3), 1.13 ms (6 of 2).  FP32 is held to 3 groups of two
+// stages by shared memory.
 #ifndef TM_STAGE_NG_F32
 #define TM_STAGE_NG_F32 3
 #endif
@@ -74,7 +85,7 @@ template <> struct StageFmt<F16> {
 #define TM_STAGE_K_F32 2
 #endif
 #ifndef TM_STAGE_NG_F16
-#define TM_STAGE_NG_F16 3
+#define TM_STAGE_NG_F16 6
 #endif
 #ifndef TM_STAGE_K_F16
 #define TM_STAGE_K_F16 2
@@ -198,6 +209,7 @@ __device__ __forceinline__ typename SpinorIO<P>::R stage_project(const unsigned 
             w[4 * k + 3] = v.w;
         }
         project_h2<MU, S>(w, h);
+        if constexpr (StageFmt<F16>::NORM == 0) return 1.f;   // the caller multiplies by the site norm
         const int np = q.box == B_XM ? 4 * q.pos + 3 : q.box == B_XP ? 4 * q.pos : q.pos;
         return reinterpret_cast<const float *>(st + StageCfg<F16, 12>::NORM_OFF)[nbox_first(q.box) + np];
     } else
@@ -221,17 +233,18 @@ __device__ __forceinline__ typename SpinorIO<P>::R stage_project(const unsigned 
 // antiperiodic boundary.
 template <int P, int RECON, int MU>
 __device__ __forceinline__ void stage_dir(const Nbrs &n, const StagedLinks<P, RECON> &src, const unsigned char *st,
-                                          SPos qf, SPos qb, unsigned neg, Spinor<typename SpinorIO<P>::R> &acc)
+                                          SPos qf, SPos qb, unsigned neg, Spinor<typename SpinorIO<P>::R> &acc,
+                                          typename SpinorIO<P>::R nf = 1, typename SpinorIO<P>::R nb = 1)
 {
     using R = typename SpinorIO<P>::R;
     Half<R> h, r;
     Link<R> u;
-    R w = stage_project<P, MU, -1>(st, qf, h);
+    R w = nf * stage_project<P, MU, -1>(st, qf, h);
     src.template fwd<MU>(n, u);
     link_mul<false>(u, h, r);
     if (neg & (1u << MU)) w = -w;
     accumulate<MU, -1>(r, w, acc);
-    w = stage_project<P, MU, +1>(st, qb, h);
+    w = nb * stage_project<P, MU, +1>(st, qb, h);
     src.template bwd<MU>(n, u);
     link_mul<true>(u, h, r);
     if (neg & (16u << MU)) w = -w;
@@ -345,7 +358,7 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
     if (warp == C::NCW) {
         // ---------------- producer: one thread issues every copy
         if (lane != 0) return;
-        const int nmap = C::CH == 3 ? 2 * NSH : NSH;
+        const int nmap = StageFmt<P>::NORM ? 2 * NSH : NSH;
         for (int gi = 0; gi < ngroups; ++gi) {
             tmap_acquire(sa.lmaps + gi);
             const BGroup &G = groups[gi];
@@ -386,7 +399,7 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
                     const BoxOrigin &o = org[b];
                     tma_load5(smem_addr(st + box_first(b) * C::CH * 16), m + box_shape(b), 2 * o.x, o.y, o.z, o.t, 0,
                               fb);
-                    if constexpr (C::CH == 3) {   // FP16 site norms; x columns 4 wide at 16-byte boundaries
+                    if constexpr (StageFmt<P>::NORM) {   // FP16 site norms; x columns 4 wide at 16-byte boundaries
                         const int xn = b == B_XM ? xnm : o.x;
                         tma_load4(smem_addr(st + C::NORM_OFF + nbox_first(b) * 4), m + NSH + box_shape(b), xn, o.y,
                                   o.z, o.t, fb);
@@ -435,6 +448,17 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
             void *outp = S->f[rout];   // loaded now, used after the hop
             Spinor<R> xs;
             if (rx >= 0) SpinorIO<P>::load(S->f[rx], vh, i, xs);   // in flight during the hop
+            R nw[8];   // neighbour site norms read from memory (FP16 without staged norms), else 1
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) nw[kk] = R(1);
+            if constexpr (P == F16 && StageFmt<F16>::NORM == 0) {
+                const float *nrm = reinterpret_cast<const float *>(static_cast<const char *>(S->f[rin]) + size_t(48) * vh);
+#pragma unroll
+                for (int mu = 0; mu < 4; ++mu) {
+                    nw[2 * mu] = ld_keep(nrm + n.fwd[mu]);
+                    nw[2 * mu + 1] = ld_keep(nrm + n.bwd[mu]);
+                }
+            }
             if (!mbar_wait(full(slot), use & 1, sa.status)) return;
             const unsigned char *st = stages + slot * C::SBYTES;
             Spinor<R> acc;
@@ -442,10 +466,10 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) acc[sp][cc] = {R(0), R(0)};
-            stage_dir<P, C::LRECON, 0>(n, src, st, q[0], q[1], neg, acc);
-            stage_dir<P, C::LRECON, 1>(n, src, st, q[2], q[3], neg, acc);
-            stage_dir<P, C::LRECON, 2>(n, src, st, q[4], q[5], neg, acc);
-            stage_dir<P, C::LRECON, 3>(n, src, st, q[6], q[7], neg, acc);
+            stage_dir<P, C::LRECON, 0>(n, src, st, q[0], q[1], neg, acc, nw[0], nw[1]);
+            stage_dir<P, C::LRECON, 1>(n, src, st, q[2], q[3], neg, acc, nw[2], nw[3]);
+            stage_dir<P, C::LRECON, 2>(n, src, st, q[4], q[5], neg, acc, nw[4], nw[5]);
+            stage_dir<P, C::LRECON, 3>(n, src, st, q[6], q[7], neg, acc, nw[6], nw[7]);
             __syncwarp();
             if (lane == 0) mbar_arrive(empty(slot));   // the stage may be refilled
             Spinor<R> o;
