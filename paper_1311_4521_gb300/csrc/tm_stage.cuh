@@ -18,10 +18,11 @@
 // been brought next to the SM in one bulk transfer, instead of eight
 // independent gathers through L1 per site and right-hand side.
 //
-// Warp roles: one producer thread issues the copies; consumer groups of
-// two warps (one thread per site of the box) compute the hop of one
-// right-hand side each.  (Issuing the copies from one lane each, 9 or 18 at
-// once, was measured slower: 1.19 against 1.07 ms for FP32 launch B.)  A ring of NSTAGE stage buffers carries the
+// Warp roles: NPROD producer threads (lane 0 of their warps) issue the
+// copies, each for its own stage buffers; consumer groups of two warps (one
+// thread per site of the box) compute the hop of one right-hand side each.
+// (Issuing the copies from one lane each, 9 or 18 at once, was measured
+// slower: 1.19 against 1.07 ms for FP32 launch B.)  A ring of NSTAGE stage buffers carries the
 // right-hand sides (stage j serves consumer group j mod NG, so every group
 // has two stages: one it computes on while the other fills) with a full and
 // an empty mbarrier each; the link tile is double-buffered on its own pair of
@@ -81,6 +82,14 @@ template <> struct StageFmt<F16> {
 #ifndef TM_STAGE_NG_F32
 #define TM_STAGE_NG_F32 3
 #endif
+// Producer threads, each in its own warp: stage buffer j is always filled by
+// producer j mod NPROD, so every buffer's uses are armed in order by one
+// thread (a parity wait can tell phase k from k+1, not from k+2).  Measured
+// on 32^3x64 with 12 right-hand sides, launch B: 1 producer 1.06-1.11 ms, 2
+// 1.01 ms (FP32-12); FP16 1.16 -> 1.07 ms.
+#ifndef TM_STAGE_NPROD
+#define TM_STAGE_NPROD 2
+#endif
 #ifndef TM_STAGE_K_F32
 #define TM_STAGE_K_F32 2
 #endif
@@ -104,7 +113,9 @@ template <int P, int RECON> struct StageCfg {
     static constexpr int NG = P == F16 ? TM_STAGE_NG_F16 : TM_STAGE_NG_F32;   // consumer groups (two warps each)
     static constexpr int NSTAGE = (P == F16 ? TM_STAGE_K_F16 : TM_STAGE_K_F32) * NG;   // stages per group
     static constexpr int NCW = 2 * NG;            // consumer warps
-    static constexpr int NT = 32 * (NCW + 1);     // + the producer warp
+    static constexpr int NPROD = TM_STAGE_NPROD;  // producer warps (one issuing thread each)
+    static constexpr int NT = 32 * (NCW + NPROD);
+    static_assert(NSTAGE % NPROD == 0, "every stage buffer belongs to one producer");
     static constexpr int NBAR = 2 * NSTAGE + 4;
     static constexpr int SMEM = NSTAGE * SBYTES + 2 * LBYTES + NBAR * 8;
     static_assert(SBYTES % 128 == 0 && LBYTES % 128 == 0, "stage buffers keep 128-byte alignment");
@@ -355,9 +366,26 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
     }
     __syncthreads();
 
-    if (warp == C::NCW) {
-        // ---------------- producer: one thread issues every copy
+    if (warp >= C::NCW) {
+        // ---------------- producers: lane 0 of each producer warp issues the copies
+        // of the stage buffers j = pi (mod NPROD) and, producer 0, of the link tiles
+        const int pi = warp - C::NCW;
         if (lane != 0) return;
+        // the last use of each of this producer's buffers and of the link tiles
+        // armed so far: on a wait that runs out, the copies still in flight are
+        // waited for (bounded) before the thread leaves, so none lands in the
+        // shared memory of a finished CTA
+        int armed[C::NSTAGE];
+#pragma unroll
+        for (int j = 0; j < C::NSTAGE; ++j) armed[j] = -1;
+        int larmed[2] = {-1, -1};
+        auto drain = [&]() {
+#pragma unroll
+            for (int j = 0; j < C::NSTAGE; ++j)
+                if (armed[j] >= 0) (void)mbar_wait(full(j), unsigned(armed[j]) & 1, sa.status);
+            for (int j = 0; j < 2; ++j)
+                if (larmed[j] >= 0) (void)mbar_wait(lfull(j), unsigned(larmed[j]) & 1, sa.status);
+        };
         const int nmap = StageFmt<P>::NORM ? 2 * NSH : NSH;
         for (int gi = 0; gi < ngroups; ++gi) {
             tmap_acquire(sa.lmaps + gi);
@@ -376,10 +404,16 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
             if (!any) continue;
             const TileBox B = tile_box(G.g, G.sbz, item - G.item0);
             const int ls = int(tl & 1);
-            if (tl >= 2 && !mbar_wait(lempty(ls), ((tl - 2) >> 1) & 1, sa.status)) return;
-            mbar_expect_tx(lfull(ls), C::LBYTES);
-            tma_load5(smem_addr(ltiles + ls * C::LBYTES), sa.lmaps + gi, W * B.xh0, B.y0, B.z0, B.t0, parity * LCH,
-                      lfull(ls));
+            if (pi == 0) {   // the links of the tile: producer 0
+                if (tl >= 2 && !mbar_wait(lempty(ls), ((tl - 2) >> 1) & 1, sa.status)) {
+                    drain();
+                    return;
+                }
+                mbar_expect_tx(lfull(ls), C::LBYTES);
+                larmed[ls] = int(tl >> 1);
+                tma_load5(smem_addr(ltiles + ls * C::LBYTES), sa.lmaps + gi, W * B.xh0, B.y0, B.z0, B.t0,
+                          parity * LCH, lfull(ls));
+            }
             const int hx = G.g.hx;
             BoxOrigin org[NBOX];   // once per tile: the producer issues every copy, keep its loop short
 #pragma unroll
@@ -389,9 +423,15 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
                 if (gated(sys[G.sys0 + r].s, gate)) continue;
                 const int slot = int(u % C::NSTAGE);
                 const unsigned use = u / C::NSTAGE;
-                if (use >= 1 && !mbar_wait(empty(slot), (use - 1) & 1, sa.status)) return;
+                ++u;
+                if (slot % C::NPROD != pi) continue;
+                if (use >= 1 && !mbar_wait(empty(slot), (use - 1) & 1, sa.status)) {
+                    drain();
+                    return;
+                }
                 const unsigned fb = full(slot);
                 mbar_expect_tx(fb, C::SBYTES);
+                armed[slot] = int(use);
                 unsigned char *st = stages + slot * C::SBYTES;
                 const CUtensorMap *m = sa.smaps + (size_t(G.sys0 + r) * NROLE + rin) * (2 * NSH);
 #pragma unroll
@@ -405,7 +445,6 @@ __global__ void __launch_bounds__(StageCfg<P, RECON>::NT, 1)
                                   o.z, o.t, fb);
                     }
                 }
-                ++u;
             }
             ++tl;
         }
