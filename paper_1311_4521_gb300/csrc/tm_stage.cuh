@@ -77,10 +77,12 @@ template <> struct StageFmt<F16> {
 // filling) of the FP32 and FP16 formats.  Measured on 32^3x64 with 12
 // right-hand sides, FP16 launch B: with staged norms 1.65, 1.39, 1.49, 1.55
 // ms for 2, 3, 4, 6 groups; with norms from memory 1.38 (3 groups of 2
-// stages), 1.20 (4 of 3), 1.13 ms (6 of 2).  FP32 is held to 3 groups of two
-// stages by shared memory.
+// stages), 1.20 (4 of 3), 1.13 ms (6 of 2).  FP32 (26 KB per stage): 3
+// groups of 2 stages 1.02 ms, 4 groups of 1 stage 0.955 ms, 6 of 1 (128
+// registers, spills) 1.03 ms: with two producers refilling, a group needs no
+// second stage of its own, and the fourth group hides more latency.
 #ifndef TM_STAGE_NG_F32
-#define TM_STAGE_NG_F32 3
+#define TM_STAGE_NG_F32 4
 #endif
 // Producer threads, each in its own warp: stage buffer j is always filled by
 // producer j mod NPROD, so every buffer's uses are armed in order by one
@@ -91,7 +93,7 @@ template <> struct StageFmt<F16> {
 #define TM_STAGE_NPROD 2
 #endif
 #ifndef TM_STAGE_K_F32
-#define TM_STAGE_K_F32 2
+#define TM_STAGE_K_F32 1
 #endif
 #ifndef TM_STAGE_NG_F16
 #define TM_STAGE_NG_F16 6
